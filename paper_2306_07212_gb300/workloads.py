@@ -1,0 +1,166 @@
+"""Seeded synthetic inputs: ReLU MLPs and box domains.
+
+This module only *draws* networks, domains and request streams. It holds none
+of the extraction arithmetic, so both the CUDA path and the FP64 oracle can take
+their inputs from it without sharing any of the method.
+
+Conventions (Section 3.4, Eq. 4): a network with widths ``[D, H_1, ..., H_L]``
+has ``W[l]`` of shape ``(H_{l+1}, H_l)`` (out x in, so ``z = W x + b``) and
+``b[l]`` of length ``H_{l+1}``.  Every layer's pre-activation zero set is a
+folded hyperplane, the last (output) layer included.
+
+Draw recipe: ``numpy.random.default_rng(seed)``; weights and biases are drawn in
+the order W1, b1, W2, b2, ... as float64 standard normals scaled by
+``sqrt(2 / fan_in)`` (He-normal) and ``sqrt(bias_var)`` respectively; a bias
+variance of 0.01 gives a bias standard deviation of 0.1.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+
+
+@dataclasses.dataclass
+class Net:
+    """A ReLU MLP in float64; ``widths[0]`` is the input dimension D."""
+
+    widths: List[int]
+    W: List[np.ndarray]
+    b: List[np.ndarray]
+
+    @property
+    def D(self) -> int:
+        return int(self.widths[0])
+
+    @property
+    def L(self) -> int:
+        return len(self.widths) - 1
+
+    @property
+    def n_neurons(self) -> int:
+        return int(sum(self.widths[1:]))
+
+    def flat_params(self) -> np.ndarray:
+        """W1, b1, W2, b2, ... concatenated (row-major W)."""
+        parts = []
+        for W, b in zip(self.W, self.b):
+            parts.append(np.ascontiguousarray(W, dtype=np.float64).ravel())
+            parts.append(np.ascontiguousarray(b, dtype=np.float64).ravel())
+        return np.concatenate(parts)
+
+    def with_flat_params(self, theta: np.ndarray) -> "Net":
+        theta = np.asarray(theta, dtype=np.float64)
+        W, b, off = [], [], 0
+        for l in range(self.L):
+            o, i = self.widths[l + 1], self.widths[l]
+            W.append(theta[off:off + o * i].reshape(o, i).copy())
+            off += o * i
+            b.append(theta[off:off + o].copy())
+            off += o
+        return Net(list(self.widths), W, b)
+
+    def rounded_to_fp32(self) -> "Net":
+        return Net(list(self.widths),
+                   [w.astype(np.float32).astype(np.float64) for w in self.W],
+                   [v.astype(np.float32).astype(np.float64) for v in self.b])
+
+
+@dataclasses.dataclass
+class Box:
+    lo: np.ndarray
+    hi: np.ndarray
+
+    @staticmethod
+    def cube(D: int, half: float = 1.0) -> "Box":
+        return Box(np.full(D, -half), np.full(D, half))
+
+
+def he_normal_mlp(widths: Sequence[int], seed: int, bias_var: float = 0.01) -> Net:
+    """He-normal weights N(0, 2/fan_in) and biases N(0, bias_var), float64."""
+    rng = np.random.default_rng(seed)
+    W, b = [], []
+    for l in range(len(widths) - 1):
+        fan_in, fan_out = int(widths[l]), int(widths[l + 1])
+        W.append(rng.standard_normal((fan_out, fan_in)) * math.sqrt(2.0 / fan_in))
+        b.append(rng.standard_normal(fan_out) * math.sqrt(bias_var))
+    return Net([int(w) for w in widths], W, b)
+
+
+# --- the five workloads -----------------------------------------------------
+
+def small_d2() -> tuple:
+    """D=2, box [-1,1]^2, MLP 2-8-8-1, He-normal weights, biases N(0,0.01), seed 0."""
+    return he_normal_mlp([2, 8, 8, 1], seed=0), Box.cube(2)
+
+
+TORUS_FILE = os.path.join(_DATA, "torus_3x64x4x1.npz")
+
+
+def torus_d3() -> tuple:
+    """D=3 torus SDF net 3-64-64-64-64-1 (FP32 weights from a 2000-step Adam fit).
+
+    The weights were produced once by ``data/make_torus_net.py`` and stored;
+    they are exactly representable in float64.
+    """
+    with np.load(TORUS_FILE) as f:
+        widths = [int(x) for x in f["widths"]]
+        W = [f[f"W{l}"].astype(np.float64) for l in range(len(widths) - 1)]
+        b = [f[f"b{l}"].astype(np.float64) for l in range(len(widths) - 1)]
+    return Net(widths, W, b), Box.cube(3)
+
+
+def precision_d4(seed: int = 0) -> tuple:
+    """D=4, box [-1,1]^4, MLP 4-128-128-128-1 He-normal, rounded once to FP32."""
+    return he_normal_mlp([4, 128, 128, 128, 1], seed=seed).rounded_to_fp32(), Box.cube(4)
+
+
+def diff_d3(seed: int = 0) -> tuple:
+    """D=3, box [-1,1]^3, MLP 3-32-32-32-1 He-normal, rounded to FP32."""
+    return he_normal_mlp([3, 32, 32, 32, 1], seed=seed).rounded_to_fp32(), Box.cube(3)
+
+
+def random_mlp(D: int, depth: int, width: int, seed: int) -> tuple:
+    """A generic random net: ``depth`` hidden layers of ``width`` and one output."""
+    widths = [D] + [width] * depth + [1]
+    return he_normal_mlp(widths, seed=seed), Box.cube(D)
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival_s: float
+    net: Net
+    box: Box
+
+
+def serving_stream(n_requests: int = 2000, rate_per_s: float = 200.0, seed: int = 0,
+                   dims=(2, 3, 4), depths=(2, 3, 4, 5, 6),
+                   widths=(16, 32, 64, 128)) -> List[Request]:
+    """Poisson arrivals (exponential gaps, mean 1/rate) of random extraction requests.
+
+    Request k draws D, depth and width from its own generator seeded with k,
+    then He-normal weights (rounded to FP32) from seed k.
+    """
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate_per_s, size=n_requests)
+    t = np.cumsum(gaps) - gaps[0]
+    out = []
+    for k in range(n_requests):
+        r = np.random.default_rng(1_000_003 + k)
+        D = int(r.choice(dims))
+        depth = int(r.choice(depths))
+        width = int(r.choice(widths))
+        net = he_normal_mlp([D] + [width] * depth + [1], seed=k).rounded_to_fp32()
+        out.append(Request(k, float(t[k]), net, Box.cube(D)))
+    return out
+
+
+def torus_sdf(p: np.ndarray, R: float = 0.6, r: float = 0.25) -> np.ndarray:
+    """Signed distance to a torus around the z axis (major radius R, minor r)."""
+    q = np.sqrt(p[:, 0] ** 2 + p[:, 1] ** 2) - R
+    return np.sqrt(q ** 2 + p[:, 2] ** 2) - r
