@@ -1,0 +1,144 @@
+/* pc.h - C ABI of libpc: polyhedral-complex extraction from ReLU networks by
+ * edge subdivision (Berzins, "Polyhedral Complex Extraction from ReLU Networks
+ * using Edge Subdivision", ICML 2023), on one GB300 (sm_103a).
+ *
+ * What is computed (Sections 3.3, 3.4 and 4): a ReLU MLP with layers
+ *   x^(l) = ReLU(W^(l) x^(l-1) + b^(l)),  l = 1..L   (Eq. 4)
+ * and a box domain [lo, hi]^D induce a polyhedral complex whose cells are named
+ * by sign vectors (Eq. 1-2).  The library returns the complex's vertices,
+ * edges and the sign vector of every vertex.  Every neuron of every layer
+ * (the output layer included) contributes one folded hyperplane; each is
+ * processed in turn by steps (1)-(5) of Section 4.2.
+ *
+ * Conventions
+ *   - W^(l) is (out x in), row-major, z = W x + b.
+ *   - Network parameters are passed as ONE flat float64 array, in the order
+ *     W1, b1, W2, b2, ..., WL, bL (each W row-major).
+ *   - Sign-vector entries: the m = 2D box facets first (entry 2d: x_d - lo_d,
+ *     entry 2d+1: hi_d - x_d; + means inside), then the neurons layer by
+ *     layer.  Entry j is stored as a 2-bit code at bits 2*(j % 32) of 64-bit
+ *     word j / 32: 00 = 0 (on the hyperplane), 01 = +, 10 = -.
+ *   - Device arrays are structure-of-arrays with a leading dimension ld
+ *     (the current capacity): coordinates X[d * ld + v], sign words
+ *     SIG[w * ld + v], edge endpoints U[e] and V[e] = U[ld + e].
+ *
+ * Ownership and errors
+ *   - A context owns every device buffer it returns; pointers stay valid until
+ *     the next pc_extract or pc_destroy on that context.
+ *   - Inputs are copied at the start of pc_extract; the caller may free them
+ *     when the call returns.
+ *   - Every call returns a pc_status; nothing aborts the process.  On an
+ *     error pc_last_error() gives a message and the context is left empty
+ *     but usable.
+ *   - A context is not thread-safe: one call at a time per context.
+ */
+#ifndef PC_H_
+#define PC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pc_ctx pc_ctx;
+
+typedef enum {
+  PC_OK = 0,
+  PC_ERR_INVALID = 1,     /* bad argument or unsupported shape */
+  PC_ERR_OOM = 2,         /* device allocation failed or budget exceeded */
+  PC_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  PC_ERR_DEGENERATE = 4,  /* genericity violated (strict mode only) */
+  PC_ERR_PAIRING = 5,     /* a splitting 2-face did not occur exactly twice */
+  PC_ERR_TOO_LARGE = 6,   /* memory estimate above the budget (server) */
+  PC_ERR_TIMEOUT = 7,     /* a bounded device-side wait ran out */
+  PC_ERR_NO_TAPE = 8,     /* pc_backward without keep_tape */
+  PC_PENDING = 9          /* server: request not finished yet */
+} pc_status;
+
+typedef enum {
+  PC_PREC_FP32 = 0,   /* FP32 values, FP32 sign decisions */
+  PC_PREC_MIXED = 1,  /* FP32/3xTF32 bulk, FP64 re-evaluation of every sign
+                         whose FP32 value is within its error bound */
+  PC_PREC_FP64 = 2    /* FP64 values throughout */
+} pc_precision;
+
+typedef enum {
+  PC_EXEC_PERSISTENT = 0, /* one cooperative kernel per layer, grid barriers */
+  PC_EXEC_STEPWISE = 1    /* one kernel per step and neuron */
+} pc_exec;
+
+typedef struct {
+  int precision;          /* pc_precision */
+  int exec;               /* pc_exec */
+  int keep_tape;          /* record the interpolation tape for pc_backward */
+  int strict;             /* return PC_ERR_DEGENERATE on any genericity violation */
+  int64_t init_vcap;      /* initial vertex capacity (grown x2 on overflow) */
+  int64_t init_ecap;      /* initial edge capacity */
+  int64_t mem_budget_bytes; /* 0 = no limit */
+  double filter_kappa;    /* PC_PREC_MIXED: re-evaluate when |z| <= kappa * bound */
+} pc_options;
+
+/* Fills *opt with defaults (mixed precision, persistent execution). */
+void pc_default_options(pc_options *opt);
+
+/* Creates a context on CUDA device `device`.  opt may be NULL (defaults). */
+pc_status pc_create(pc_ctx **out, int device, const pc_options *opt);
+pc_status pc_destroy(pc_ctx *ctx);
+
+/* Optional device allocator used for every buffer of the context (for
+ * example a framework's caching allocator).  alloc returns a device pointer
+ * or NULL; stream is the cudaStream_t of the call.  Without it the context
+ * uses cudaMallocAsync / cudaFreeAsync. */
+typedef void *(*pc_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*pc_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+pc_status pc_set_allocator(pc_ctx *ctx, pc_alloc_fn alloc, pc_free_fn free_fn, void *user);
+
+/* Edge subdivision (Section 4.2): extracts the complex of the network on the
+ * box.  widths: host array of L+1 ints (widths[0] = D).  params: flat float64
+ * parameters (layout above), host or device memory.  box_lo/box_hi: host
+ * arrays of D doubles.  stream: cudaStream_t (NULL = legacy default stream).
+ * Blocks until the result is ready (one device->host status read).
+ * Limits: 1 <= D <= 8, widths <= 256, 2D + sum(widths[1..L]) <= 1024.
+ * Returns PC_ERR_PAIRING / PC_ERR_DEGENERATE (strict) when genericity fails. */
+pc_status pc_extract(pc_ctx *ctx, int L, const int32_t *widths, const double *params,
+                     const double *box_lo, const double *box_hi, void *stream);
+
+/* Counts of the last extraction: vertices, edges, 64-bit words per sign
+ * vector, input dimension D, and sign-vector entries (2D + neurons). */
+pc_status pc_counts(pc_ctx *ctx, int64_t *n_vertices, int64_t *n_edges, int32_t *sig_words,
+                    int32_t *dim, int32_t *n_entries);
+
+/* Vertex coordinates, float64, SoA X[d * ld + v].  *dev and *ld receive the
+ * device array (either may be NULL); if out != NULL the D x nV block is copied
+ * to out (host or device memory, row d at out + d * nV). */
+pc_status pc_vertices(pc_ctx *ctx, const double **dev, int64_t *ld, double *out);
+
+/* Edges, int32 vertex indices U[e], V[e] = U[ld + e]; out (nullable) receives
+ * 2 x nE (row 0 = first endpoints, row 1 = second endpoints). */
+pc_status pc_edges(pc_ctx *ctx, const int32_t **dev, int64_t *ld, int32_t *out);
+
+/* Packed sign vectors, SIG[w * ld + v]; out (nullable) receives S x nV. */
+pc_status pc_signvectors(pc_ctx *ctx, const uint64_t **dev, int64_t *ld, uint64_t *out);
+
+/* Per-neuron counters of the last extraction, host array of n_neurons x 8
+ * int64: vertices before, edges before, splitting edges, 2-face keys, paired
+ * faces, FP64 re-evaluations, undecidable signs, genericity violations. */
+pc_status pc_stats(pc_ctx *ctx, int64_t *out, int n_neurons);
+
+/* Adjoint of the vertex coordinates with respect to the parameters, through
+ * the interpolation formula of step (4) and the per-layer forward products of
+ * step (1).  grad_x: D x nV float64 (row d at grad_x + d * nV), host or device.
+ * grad_params: flat float64 array in the parameter layout, host or device;
+ * overwritten.  Needs keep_tape = 1 at extraction (else PC_ERR_NO_TAPE). */
+pc_status pc_backward(pc_ctx *ctx, const double *grad_x, double *grad_params, void *stream);
+
+/* Message of the last error on this context ("" if none). */
+const char *pc_last_error(pc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PC_H_ */

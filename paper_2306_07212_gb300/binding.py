@@ -1,0 +1,234 @@
+"""Thin Python binding of libpc (include/pc.h) over ctypes.
+
+Argument marshalling only: every step of the extraction runs in the CUDA
+library.  PyTorch is used for device memory (the library's buffers come from
+torch's caching allocator through pc_set_allocator) and for streams.  There is
+no CPU fallback: if the compiled library is missing, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from .buildlib import LIB
+
+PC_OK = 0
+STATUS_NAMES = {0: "PC_OK", 1: "PC_ERR_INVALID", 2: "PC_ERR_OOM", 3: "PC_ERR_CUDA",
+                4: "PC_ERR_DEGENERATE", 5: "PC_ERR_PAIRING", 6: "PC_ERR_TOO_LARGE",
+                7: "PC_ERR_TIMEOUT", 8: "PC_ERR_NO_TAPE", 9: "PC_PENDING"}
+PRECISION = {"fp32": 0, "mixed": 1, "fp64": 2}
+EXEC = {"persistent": 0, "stepwise": 1}
+
+# Every symbol include/pc.h declares (checked by the tests).
+EXPORTS = ["pc_default_options", "pc_create", "pc_destroy", "pc_set_allocator", "pc_extract",
+           "pc_counts", "pc_vertices", "pc_edges", "pc_signvectors", "pc_stats", "pc_backward",
+           "pc_last_error"]
+
+
+class PcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("exec", ctypes.c_int), ("keep_tape", ctypes.c_int),
+                ("strict", ctypes.c_int), ("init_vcap", ctypes.c_int64), ("init_ecap", ctypes.c_int64),
+                ("mem_budget_bytes", ctypes.c_int64), ("filter_kappa", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB):
+    """Loads libpc.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        vp, i64p, i32p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)
+        lib.pc_default_options.argtypes = [ctypes.POINTER(Options)]
+        lib.pc_default_options.restype = None
+        lib.pc_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(Options)]
+        lib.pc_destroy.argtypes = [vp]
+        lib.pc_set_allocator.argtypes = [vp, ALLOC_FN, FREE_FN, vp]
+        lib.pc_extract.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp]
+        lib.pc_counts.argtypes = [vp, i64p, i64p, i32p, i32p, i32p]
+        lib.pc_vertices.argtypes = [vp, ctypes.POINTER(vp), i64p, vp]
+        lib.pc_edges.argtypes = [vp, ctypes.POINTER(vp), i64p, vp]
+        lib.pc_signvectors.argtypes = [vp, ctypes.POINTER(vp), i64p, vp]
+        lib.pc_stats.argtypes = [vp, i64p, ctypes.c_int]
+        lib.pc_backward.argtypes = [vp, vp, vp, vp]
+        lib.pc_last_error.argtypes = [vp]
+        lib.pc_last_error.restype = ctypes.c_char_p
+        for f in EXPORTS:
+            if f not in ("pc_default_options", "pc_last_error"):
+                getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _addr(x) -> Optional[int]:
+    """Address of a numpy array or torch tensor (host or device)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x.data_ptr())
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+class Extractor:
+    """One libpc context: extract complexes of ReLU MLPs on a box.
+
+    precision: "fp32" | "mixed" (FP32 bulk, FP64 re-evaluation of signs within
+    the FP32 error bound) | "fp64".  execution: "persistent" (one cooperative
+    kernel per layer) | "stepwise" (one kernel per step and neuron).
+    """
+
+    def __init__(self, device: int = 0, precision: str = "mixed", execution: str = "persistent",
+                 keep_tape: bool = False, strict: bool = False, init_vcap: int = 0, init_ecap: int = 0,
+                 mem_budget_bytes: int = 0, kappa: float = 2.0, torch_allocator: bool = True):
+        self._lib = load_library()
+        o = Options()
+        self._lib.pc_default_options(ctypes.byref(o))
+        o.precision = PRECISION[precision]
+        o.exec = EXEC[execution]
+        o.keep_tape = int(keep_tape)
+        o.strict = int(strict)
+        o.init_vcap, o.init_ecap = int(init_vcap), int(init_ecap)
+        o.mem_budget_bytes = int(mem_budget_bytes)
+        o.filter_kappa = float(kappa)
+        self.device = device
+        self.options = o
+        self._ctx = ctypes.c_void_p()
+        self._check(self._lib.pc_create(ctypes.byref(self._ctx), device, ctypes.byref(o)))
+        self._cb = None
+        if torch_allocator:
+            import torch
+
+            def _alloc(size, stream, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(size), device, int(stream or 0))
+                except Exception:
+                    return None
+
+            def _free(ptr, size, stream, user):
+                try:
+                    torch.cuda.caching_allocator_delete(int(ptr))
+                except Exception:
+                    pass
+
+            self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))
+            self._check(self._lib.pc_set_allocator(self._ctx, self._cb[0], self._cb[1], None))
+        self.net = None
+
+    def _check(self, st: int):
+        if st != PC_OK:
+            msg = self._lib.pc_last_error(self._ctx).decode() if getattr(self, "_ctx", None) else ""
+            raise PcError(st, msg)
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self._lib.pc_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- extraction -----------------------------------------------------------
+    def extract(self, net, box, params=None, stream=None) -> "Extractor":
+        """Runs pc_extract.  params: optional flat float64 parameters already
+        on the device (torch tensor); else net.flat_params() from the host."""
+        widths = np.ascontiguousarray(net.widths, np.int32)
+        if params is None:
+            params = np.ascontiguousarray(net.flat_params(), np.float64)
+        lo = np.ascontiguousarray(box.lo, np.float64)
+        hi = np.ascontiguousarray(box.hi, np.float64)
+        self._keep = (widths, params, lo, hi)
+        self.net = net
+        st = self._lib.pc_extract(self._ctx, len(net.widths) - 1, _addr(widths), _addr(params),
+                                  _addr(lo), _addr(hi), _stream_handle(stream))
+        self._check(st)
+        return self
+
+    def counts(self) -> dict:
+        nv, ne = ctypes.c_int64(), ctypes.c_int64()
+        sw, dim, nent = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.pc_counts(self._ctx, ctypes.byref(nv), ctypes.byref(ne), ctypes.byref(sw),
+                                        ctypes.byref(dim), ctypes.byref(nent)))
+        return {"nV": nv.value, "nE": ne.value, "S": sw.value, "D": dim.value, "P": nent.value}
+
+    def vertices(self) -> np.ndarray:
+        """(nV, D) float64 host copy."""
+        c = self.counts()
+        out = np.empty((c["D"], c["nV"]), np.float64)
+        self._check(self._lib.pc_vertices(self._ctx, None, None, _addr(out)))
+        return out.T
+
+    def edges(self) -> np.ndarray:
+        """(nE, 2) int32 host copy."""
+        c = self.counts()
+        out = np.empty((2, c["nE"]), np.int32)
+        self._check(self._lib.pc_edges(self._ctx, None, None, _addr(out)))
+        return np.ascontiguousarray(out.T)
+
+    def sign_words(self) -> np.ndarray:
+        """(S, nV) uint64 packed sign vectors, host copy."""
+        c = self.counts()
+        out = np.empty((c["S"], c["nV"]), np.uint64)
+        self._check(self._lib.pc_signvectors(self._ctx, None, None, _addr(out)))
+        return out
+
+    def stats(self) -> np.ndarray:
+        """(N, 8) int64: V before, E before, splits, keys, pairs, filtered, undecided, degenerate."""
+        N = int(sum(self.net.widths[1:]))
+        out = np.zeros((N, 8), np.int64)
+        self._check(self._lib.pc_stats(self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), N))
+        return out
+
+    def device_arrays(self):
+        """(X ptr, ld), (E ptr, ld), (SIG ptr, ld) of the context's device buffers."""
+        res = []
+        for f in (self._lib.pc_vertices, self._lib.pc_edges, self._lib.pc_signvectors):
+            p, ld = ctypes.c_void_p(), ctypes.c_int64()
+            self._check(f(self._ctx, ctypes.byref(p), ctypes.byref(ld), None))
+            res.append((p.value, ld.value))
+        return res
+
+    def vertices_into(self, out) -> None:
+        """Copies the D x nV coordinate block into `out` (host or device memory)."""
+        self._check(self._lib.pc_vertices(self._ctx, None, None, _addr(out)))
+
+    def backward(self, grad_x, grad_params, stream=None) -> None:
+        """pc_backward: grad_x (D, nV) float64, grad_params flat float64 (host or device)."""
+        self._check(self._lib.pc_backward(self._ctx, _addr(grad_x), _addr(grad_params), _stream_handle(stream)))

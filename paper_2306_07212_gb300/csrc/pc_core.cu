@@ -1,0 +1,720 @@
+// libpc core: device state management, the layer-start forward product
+// (step (1) of Section 4.2), the per-neuron phase kernels in both execution
+// modes, and the C ABI declared in include/pc.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pc.h"
+#include "pc_ctx.h"
+#include "pc_phases.cuh"
+
+namespace pc {
+
+// ---------------------------------------------------------------------------
+// Set-up kernels
+
+// float32 copy of the parameters and per-layer norms used by the FP32 error
+// bound: max_j sum_k |W_jk| and max_j |b_j| (rounded up).
+__global__ void k_prep(NetDesc net, float* W32, float* norms, long long n_params) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n_params;
+       t += (long long)gridDim.x * blockDim.x)
+    W32[t] = static_cast<float>(net.W64[t]);
+  if (blockIdx.x < net.L) {
+    const int l = blockIdx.x, H = net.w[l + 1], K = net.w[l];
+    __shared__ double s_w[256], s_b[256];
+    double mw = 0.0, mb = 0.0;
+    for (int j = threadIdx.x; j < H; j += blockDim.x) {
+      double s = 0.0;
+      for (int k = 0; k < K; ++k) s += fabs(net.W64[net.wofs[l] + (long long)j * K + k]);
+      mw = fmax(mw, s);
+      mb = fmax(mb, fabs(net.W64[net.bofs[l] + j]));
+    }
+    s_w[threadIdx.x] = mw;
+    s_b[threadIdx.x] = mb;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 1; q < blockDim.x; ++q) {
+        mw = fmax(mw, s_w[q]);
+        mb = fmax(mb, s_b[q]);
+      }
+      norms[2 * l] = __double2float_ru(mw * (1.0 + 1e-6));
+      norms[2 * l + 1] = __double2float_ru(mb);
+    }
+  }
+}
+
+// Step 0: the box's 2^D corners and D 2^(D-1) edges; boundary entries first
+// (entry 2d: x_d - lo_d, 2d+1: hi_d - x_d), every neuron entry unprocessed.
+__global__ void k_init(NetDesc net, State st) {
+  const int D = net.D, nc = 1 << D, ne0 = D << (D - 1);
+  const long long Vcap = st.Vcap;
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    uint64_t w0 = 0;
+    for (int d = 0; d < D; ++d) {
+      const bool up = (c >> d) & 1;
+      st.X[(long long)d * Vcap + c] = up ? net.hi[d] : net.lo[d];
+      if (up) w0 |= kPlus << (2 * (2 * d));
+      else w0 |= kPlus << (2 * (2 * d + 1));
+    }
+    st.SIG[c] = w0;
+    for (int w = 1; w < net.S; ++w) st.SIG[(long long)w * Vcap + c] = 0;
+  }
+  for (int e = threadIdx.x; e < ne0; e += blockDim.x) {
+    const int d = e >> (D - 1), r = e & ((1 << (D - 1)) - 1);
+    const int c = ((r >> d) << (d + 1)) | (r & ((1 << d) - 1));
+    st.EU[e] = c;
+    st.EW[e] = c | (1 << d);
+  }
+  if (threadIdx.x == 0) {
+    Counters c0{};
+    c0.nV_before = nc;
+    c0.nE_before = ne0;
+    st.cnt[0] = c0;
+    Global g{};
+    g.halted_at = -1;
+    *st.g = g;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Step (1) at the start of layer l: Z_l = W_l a + b_l for every vertex, with
+// a = x (l = 0) or a_k = z_k of layer l-1 if the vertex's entry is + else 0.
+// SIMT version: one thread per vertex and 16 output neurons per block row.
+template <typename ZT, bool MIXED>
+__global__ void __launch_bounds__(128) k_gemm_simt(NetDesc net, State st, int l) {
+  constexpr int TJ = 16;
+  if (st.g->halted_at >= 0 || (st.g->error & kErrTimeout)) return;
+  const Counters* c = st.cnt + net.off[l];
+  const long long nV = c->nV_before + c->nsplit;
+  const int H = net.w[l + 1], K = net.w[l];
+  const int j0 = blockIdx.y * TJ;
+  __shared__ ZT Ws[TJ][kMaxWidth + 1];
+  __shared__ double Wd[TJ][kMaxD];
+  __shared__ ZT bs[TJ];
+  __shared__ double bd[TJ];
+  for (int t = threadIdx.x; t < TJ * K; t += blockDim.x) {
+    const int jj = t / K, kk = t % K, j = j0 + jj;
+    const double wv = j < H ? net.W64[net.wofs[l] + (long long)j * K + kk] : 0.0;
+    Ws[jj][kk] = static_cast<ZT>(wv);
+    if (kk < kMaxD) Wd[jj][kk] = wv;
+  }
+  if (threadIdx.x < TJ) {
+    const int j = j0 + threadIdx.x;
+    const double bv = j < H ? net.W64[net.bofs[l] + j] : 0.0;
+    bs[threadIdx.x] = static_cast<ZT>(bv);
+    bd[threadIdx.x] = bv;
+  }
+  __syncthreads();
+  const long long Vcap = st.Vcap;
+  ZT* Zout = static_cast<ZT*>(st.Z[l & 1]);
+  const ZT* Zin = static_cast<const ZT*>(st.Z[(l + 1) & 1]);
+  const int ebase = net.m + (l > 0 ? net.off[l - 1] : 0);
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nV;
+       v += (long long)gridDim.x * blockDim.x) {
+    ZT acc[TJ];
+    float amax = 0.f;
+    if (l == 0) {
+      double dacc[TJ];
+#pragma unroll
+      for (int jj = 0; jj < TJ; ++jj) dacc[jj] = bd[jj];
+      for (int d = 0; d < K; ++d) {
+        const double x = st.X[(long long)d * Vcap + v];
+        amax = fmaxf(amax, static_cast<float>(fabs(x)));
+#pragma unroll
+        for (int jj = 0; jj < TJ; ++jj) dacc[jj] = fma(Wd[jj][d], x, dacc[jj]);
+      }
+#pragma unroll
+      for (int jj = 0; jj < TJ; ++jj) acc[jj] = static_cast<ZT>(dacc[jj]);
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < TJ; ++jj) acc[jj] = bs[jj];
+      uint64_t word = 0;
+      int cw = -1;
+      for (int kk = 0; kk < K; ++kk) {
+        const int entry = ebase + kk, wi = entry >> 5;
+        if (wi != cw) {
+          word = st.SIG[(long long)wi * Vcap + v];
+          cw = wi;
+        }
+        const bool act = ((word >> (2 * (entry & 31))) & 3ull) == kPlus;
+        const ZT a = act ? Zin[(long long)kk * Vcap + v] : ZT(0);
+        amax = fmaxf(amax, fabsf(static_cast<float>(a)));
+#pragma unroll
+        for (int jj = 0; jj < TJ; ++jj) acc[jj] = fma(Ws[jj][kk], a, acc[jj]);
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < TJ; ++jj)
+      if (j0 + jj < H) Zout[(long long)(j0 + jj) * Vcap + v] = acc[jj];
+    if (MIXED && blockIdx.y == 0) {
+      const float wn = net.norms[2 * l], bm = net.norms[2 * l + 1];
+      if (l == 0) st.esc[v] = 1.2e-7f * (wn * amax + bm);
+      else st.esc[v] = float(K + 4) * 1.2e-7f * (wn * amax + bm) + wn * st.esc[v];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Neuron phases: stepwise kernels and the persistent per-layer kernel.
+
+__device__ __forceinline__ bool stopped(const State& st) {
+  return st.g->halted_at >= 0 || (st.g->error & kErrTimeout);
+}
+
+template <typename ZT, bool MIXED>
+__global__ void __launch_bounds__(kBlock) k_sign(NetDesc net, State st, int l, int i, int mw, int res_warps) {
+  extern __shared__ double dsm[];
+  __shared__ Smem sm;
+  if (stopped(st)) return;
+  phase_sign<ZT, MIXED>(net, st, l & 1, l, i, net.off[l] + i, sm, dsm, mw, res_warps);
+}
+
+__global__ void __launch_bounds__(kBlock) k_edges(NetDesc net, State st, int l, int i) {
+  __shared__ Smem sm;
+  if (stopped(st)) return;
+  phase_edges(net, st, net.off[l] + i, sm);
+}
+
+template <typename ZT, bool MIXED>
+__global__ void __launch_bounds__(kBlock) k_split(NetDesc net, State st, int l, int i) {
+  __shared__ Smem sm;
+  if (stopped(st)) return;
+  phase_split<ZT, MIXED>(net, st, l & 1, l, i, net.off[l] + i, sm);
+}
+
+template <typename ZT, bool MIXED>
+__global__ void __launch_bounds__(kBlock) k_layer(NetDesc net, State st, int l, int i_begin, int mw,
+                                                   int res_warps) {
+  extern __shared__ double dsm[];
+  __shared__ Smem sm;
+  if (stopped(st)) return;
+  unsigned int passed = 0;
+  const int H = net.w[l + 1];
+  for (int i = i_begin; i < H; ++i) {
+    const int n = net.off[l] + i;
+    phase_sign<ZT, MIXED>(net, st, l & 1, l, i, n, sm, dsm, mw, res_warps);
+    if (!grid_barrier(st.g, passed)) return;
+    phase_edges(net, st, n, sm);
+    if (!grid_barrier(st.g, passed)) return;
+    if (phase_split<ZT, MIXED>(net, st, l & 1, l, i, n, sm)) return;
+    if (!grid_barrier(st.g, passed)) return;
+  }
+}
+
+}  // namespace pc
+
+using namespace pc;
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+void* ctx_alloc(pc_ctx* c, size_t bytes) {
+  bytes = round_up(std::max<size_t>(bytes, 256), 256);
+  if (c->opt.mem_budget_bytes > 0 && c->allocated + bytes > (size_t)c->opt.mem_budget_bytes) return nullptr;
+  void* p = nullptr;
+  if (c->alloc_fn) {
+    p = c->alloc_fn(bytes, c->stream, c->alloc_user);
+  } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    c->allocated += bytes;
+    c->sizes[p] = bytes;
+  }
+  return p;
+}
+
+void ctx_free(pc_ctx* c, void*& p) {
+  if (!p) return;
+  auto it = c->sizes.find(p);
+  const size_t bytes = it != c->sizes.end() ? it->second : 0;
+  if (it != c->sizes.end()) c->sizes.erase(it);
+  c->allocated -= bytes;
+  if (c->free_fn) c->free_fn(p, bytes, c->stream, c->alloc_user);
+  else cudaFreeAsync(p, c->stream);
+  p = nullptr;
+}
+
+#define PC_CUDA(call)                                                          \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) {                                                   \
+      throw PcError(PC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                          \
+  } while (0)
+
+static size_t zsize_of(int prec) { return prec == PC_PREC_FP64 ? 8 : 4; }
+
+// (Re)allocates the state for capacities (V, E, T, tape); copies live data.
+static void realloc_state(pc_ctx* c, long long V, long long E, long long T, bool copy) {
+  const int D = c->net.D, S = c->net.S, Hm = c->hmax;
+  const size_t zs = zsize_of(c->net.precision);
+  StateBufs nb;
+  auto A = [&](void*& p, size_t bytes) {
+    p = ctx_alloc(c, bytes);
+    if (!p) throw PcError(PC_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  };
+  A(nb.X, sizeof(double) * D * V);
+  A(nb.Z[0], zs * Hm * V);
+  A(nb.Z[1], zs * Hm * V);
+  A(nb.esc, sizeof(float) * V);
+  A(nb.SIG, sizeof(uint64_t) * S * V);
+  A(nb.E, sizeof(int32_t) * 2 * E);
+  A(nb.stage, sizeof(int32_t) * E);
+  A(nb.table, sizeof(uint64_t) * T);
+  if (c->opt.keep_tape) {
+    A(nb.tape_pq, sizeof(int32_t) * 2 * V);
+    A(nb.tape_t, sizeof(double) * V);
+  }
+  PC_CUDA(cudaMemsetAsync(nb.table, 0xff, sizeof(uint64_t) * T, c->stream));
+  StateBufs& ob = c->bufs;
+  if (copy && ob.X) {
+    const long long oV = c->Vcap, oE = c->Ecap, nV = std::min(oV, V), nE = std::min(oE, E);
+    auto cp2 = [&](void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, size_t rows) {
+      if (rows && width) PC_CUDA(cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, cudaMemcpyDeviceToDevice, c->stream));
+    };
+    cp2(nb.X, 8 * V, ob.X, 8 * oV, 8 * nV, D);
+    cp2(nb.Z[0], zs * V, ob.Z[0], zs * oV, zs * nV, Hm);
+    cp2(nb.Z[1], zs * V, ob.Z[1], zs * oV, zs * nV, Hm);
+    cp2(nb.esc, 4 * V, ob.esc, 4 * oV, 4 * nV, 1);
+    cp2(nb.SIG, 8 * V, ob.SIG, 8 * oV, 8 * nV, S);
+    cp2(nb.E, 4 * E, ob.E, 4 * oE, 4 * nE, 2);
+    if (c->opt.keep_tape && ob.tape_pq) {
+      cp2(nb.tape_pq, 4 * V, ob.tape_pq, 4 * oV, 4 * nV, 2);
+      cp2(nb.tape_t, 8 * V, ob.tape_t, 8 * oV, 8 * nV, 1);
+    }
+  }
+  ob.release(c);
+  c->bufs = nb;
+  c->Vcap = V;
+  c->Ecap = E;
+  c->Tcap = T;
+}
+
+static void ensure_fixed(pc_ctx* c, int N) {
+  const size_t cnt_bytes = sizeof(Counters) * (N + 1);
+  if (c->cnt_slots < N + 1) {
+    ctx_free(c, c->cnt);
+    c->cnt = ctx_alloc(c, cnt_bytes);
+    if (!c->cnt) throw PcError(PC_ERR_OOM, "counter allocation failed");
+    if (c->h_cnt) cudaFreeHost(c->h_cnt);
+    PC_CUDA(cudaMallocHost(&c->h_cnt, cnt_bytes));
+    c->cnt_slots = N + 1;
+  }
+  if (!c->g) {
+    c->g = ctx_alloc(c, sizeof(Global));
+    c->cta = ctx_alloc(c, sizeof(long long) * kMaxGrid);
+    if (!c->g || !c->cta) throw PcError(PC_ERR_OOM, "allocation failed");
+    PC_CUDA(cudaMallocHost(&c->h_g, sizeof(Global)));
+  }
+}
+
+static State make_state(pc_ctx* c) {
+  State s{};
+  s.Vcap = c->Vcap;
+  s.Ecap = c->Ecap;
+  s.Tcap = c->Tcap;
+  s.X = static_cast<double*>(c->bufs.X);
+  s.Z[0] = c->bufs.Z[0];
+  s.Z[1] = c->bufs.Z[1];
+  s.esc = static_cast<float*>(c->bufs.esc);
+  s.SIG = static_cast<uint64_t*>(c->bufs.SIG);
+  s.EU = static_cast<int32_t*>(c->bufs.E);
+  s.EW = s.EU + c->Ecap;
+  s.stage = static_cast<int32_t*>(c->bufs.stage);
+  s.table = static_cast<uint64_t*>(c->bufs.table);
+  s.cnt = static_cast<Counters*>(c->cnt);
+  s.g = static_cast<Global*>(c->g);
+  s.cta_count = static_cast<long long*>(c->cta);
+  s.tape_pq = static_cast<int32_t*>(c->bufs.tape_pq);
+  s.tape_t = static_cast<double*>(c->bufs.tape_t);
+  s.tape_cap = c->opt.keep_tape ? c->Vcap : 0;
+  s.keep_tape = c->opt.keep_tape;
+  return s;
+}
+
+template <typename ZT, bool MIXED>
+struct Kernels {
+  static void gemm(pc_ctx* c, const State& st, int l) {
+    const int H = c->net.w[l + 1];
+    dim3 grid(std::max(1, std::min<int>(c->num_sms * 8, int((c->Vcap + 127) / 128))), (H + 15) / 16);
+    k_gemm_simt<ZT, MIXED><<<grid, 128, 0, c->stream>>>(c->net, st, l);
+    PC_CUDA(cudaGetLastError());
+  }
+  static void layer(pc_ctx* c, const State& st, int l, int i_begin) {
+    const int H = c->net.w[l + 1];
+    if (c->opt.exec == PC_EXEC_PERSISTENT) {
+      PC_CUDA(cudaMemsetAsync(&static_cast<Global*>(c->g)->barrier, 0, sizeof(unsigned int), c->stream));
+      auto fn = k_layer<ZT, MIXED>;
+      NetDesc net = c->net;
+      State s = st;
+      int l_ = l, ib = i_begin, mw = c->mw, rw = c->res_warps;
+      void* args[] = {&net, &s, &l_, &ib, &mw, &rw};
+      PC_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(c->grid_persist), dim3(kBlock), args,
+                                          c->res_smem, c->stream));
+    } else {
+      for (int i = i_begin; i < H; ++i) {
+        k_sign<ZT, MIXED><<<c->grid_step, kBlock, c->res_smem, c->stream>>>(c->net, st, l, i, c->mw, c->res_warps);
+        k_edges<<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l, i);
+        k_split<ZT, MIXED><<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l, i);
+      }
+      PC_CUDA(cudaGetLastError());
+    }
+  }
+  static int occupancy(pc_ctx* c) {
+    int nb = 0;
+    PC_CUDA(cudaFuncSetAttribute(k_layer<ZT, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->res_smem));
+    PC_CUDA(cudaFuncSetAttribute(k_sign<ZT, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->res_smem));
+    PC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_layer<ZT, MIXED>, kBlock, c->res_smem));
+    return nb;
+  }
+};
+
+template <typename ZT, bool MIXED>
+static void enqueue(pc_ctx* c, int l0, int i0, bool gemm_done) {
+  const State st = make_state(c);
+  for (int l = l0; l < c->net.L; ++l) {
+    if (!(l == l0 && gemm_done)) Kernels<ZT, MIXED>::gemm(c, st, l);
+    Kernels<ZT, MIXED>::layer(c, st, l, l == l0 ? i0 : 0);
+  }
+}
+
+static void enqueue_any(pc_ctx* c, int l0, int i0, bool gemm_done) {
+  switch (c->net.precision) {
+    case PC_PREC_FP64: enqueue<double, false>(c, l0, i0, gemm_done); break;
+    case PC_PREC_FP32: enqueue<float, false>(c, l0, i0, gemm_done); break;
+    default: enqueue<float, true>(c, l0, i0, gemm_done); break;
+  }
+}
+
+static int occupancy_any(pc_ctx* c) {
+  switch (c->net.precision) {
+    case PC_PREC_FP64: return Kernels<double, false>::occupancy(c);
+    case PC_PREC_FP32: return Kernels<float, false>::occupancy(c);
+    default: return Kernels<float, true>::occupancy(c);
+  }
+}
+
+static long long pow2_at_least(long long x) {
+  long long p = 64;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* params,
+                        const double* lo, const double* hi) {
+  if (L < 1 || L > kMaxL) throw PcError(PC_ERR_INVALID, "number of layers must be in [1, 16]");
+  const int D = widths[0];
+  if (D < 1 || D > kMaxD) throw PcError(PC_ERR_INVALID, "input dimension must be in [1, 8]");
+  NetDesc& net = c->net;
+  net = NetDesc{};
+  net.L = L;
+  net.D = D;
+  net.m = 2 * D;
+  net.precision = c->opt.precision;
+  net.kappa = static_cast<float>(c->opt.filter_kappa > 0 ? c->opt.filter_kappa : 2.0);
+  long long p = 0;
+  int n = 0, hmax = 0, mw = D;
+  for (int l = 0; l <= L; ++l) {
+    if (widths[l] < 1 || widths[l] > kMaxWidth) throw PcError(PC_ERR_INVALID, "layer widths must be in [1, 256]");
+    net.w[l] = widths[l];
+  }
+  for (int l = 0; l < L; ++l) {
+    net.off[l] = n;
+    net.wofs[l] = p;
+    p += (long long)widths[l + 1] * widths[l];
+    net.bofs[l] = p;
+    p += widths[l + 1];
+    n += widths[l + 1];
+    hmax = std::max(hmax, widths[l + 1]);
+    mw = std::max(mw, widths[l + 1]);
+  }
+  net.off[L] = n;
+  net.N = n;
+  net.P = net.m + n;
+  if (net.P > kMaxEntries) throw PcError(PC_ERR_INVALID, "2D + number of neurons must be <= 1024");
+  net.S = (net.P + 31) / 32;
+  for (int d = 0; d < D; ++d) {
+    net.lo[d] = lo[d];
+    net.hi[d] = hi[d];
+    if (!(hi[d] > lo[d])) throw PcError(PC_ERR_INVALID, "box must have hi > lo");
+  }
+  c->hmax = hmax;
+  c->mw = mw;
+  c->N = n;
+
+  // parameters: device copies in float64 and float32, per-layer norms
+  const size_t pbytes = sizeof(double) * p;
+  if (c->params_cap < p) {
+    ctx_free(c, c->params64);
+    ctx_free(c, c->params32);
+    ctx_free(c, c->norms);
+    c->params64 = ctx_alloc(c, pbytes);
+    c->params32 = ctx_alloc(c, sizeof(float) * p);
+    c->norms = ctx_alloc(c, sizeof(float) * 2 * kMaxL);
+    if (!c->params64 || !c->params32 || !c->norms) throw PcError(PC_ERR_OOM, "parameter allocation failed");
+    c->params_cap = p;
+  }
+  PC_CUDA(cudaMemcpyAsync(c->params64, params, pbytes, cudaMemcpyDefault, c->stream));
+  net.W64 = static_cast<const double*>(c->params64);
+  net.W32 = static_cast<const float*>(c->params32);
+  net.norms = static_cast<const float*>(c->norms);
+  k_prep<<<std::max(L, 64), 256, 0, c->stream>>>(net, static_cast<float*>(c->params32), static_cast<float*>(c->norms), p);
+  PC_CUDA(cudaGetLastError());
+
+  // state buffers (kept across extractions when shapes allow)
+  ensure_fixed(c, n);
+  const size_t zs = zsize_of(net.precision);
+  const bool reshape = !c->bufs.X || c->shape_D != D || c->shape_S < net.S || c->shape_H < hmax ||
+                       c->shape_zs != zs || c->shape_tape != c->opt.keep_tape;
+  if (reshape) {
+    long long V = std::max<long long>(c->Vcap, std::max<long long>(c->opt.init_vcap, 1 << 14));
+    long long E = std::max<long long>(c->Ecap, std::max<long long>(c->opt.init_ecap, (long long)D * V));
+    long long T = std::max<long long>(c->Tcap, 1 << 16);
+    c->bufs.release(c);
+    c->shape_D = D;
+    c->shape_S = net.S;
+    c->shape_H = hmax;
+    c->shape_zs = zs;
+    c->shape_tape = c->opt.keep_tape;
+    realloc_state(c, V, E, T, false);
+  } else {
+    PC_CUDA(cudaMemsetAsync(c->bufs.table, 0xff, sizeof(uint64_t) * c->Tcap, c->stream));
+  }
+  PC_CUDA(cudaMemsetAsync(c->cnt, 0, sizeof(Counters) * (n + 1), c->stream));
+
+  // launch geometry
+  const int ws = resolve_ws_doubles(mw, D);
+  c->res_warps = std::max(1, std::min(4, int((64 * 1024) / (ws * 8))));
+  c->res_smem = (size_t)c->res_warps * ws * 8;
+  const int occ = occupancy_any(c);
+  if (occ < 1) throw PcError(PC_ERR_INVALID, "persistent kernel does not fit on an SM");
+  c->grid_persist = std::min(kMaxGrid, occ * c->num_sms);
+  c->grid_step = std::min(kMaxGrid, 2 * c->num_sms);
+
+  k_init<<<1, 256, 0, c->stream>>>(net, make_state(c));
+  PC_CUDA(cudaGetLastError());
+
+  int l0 = 0, i0 = 0;
+  bool gemm_done = false;
+  for (int attempt = 0;; ++attempt) {
+    enqueue_any(c, l0, i0, gemm_done);
+    PC_CUDA(cudaMemcpyAsync(c->h_g, c->g, sizeof(Global), cudaMemcpyDeviceToHost, c->stream));
+    PC_CUDA(cudaStreamSynchronize(c->stream));
+    Global g = *static_cast<Global*>(c->h_g);
+    if (g.error & kErrTimeout) throw PcError(PC_ERR_TIMEOUT, "a device-side grid barrier timed out");
+    if (g.halted_at < 0) break;
+    if (attempt > 60) throw PcError(PC_ERR_OOM, "capacity growth did not converge");
+    // grow what ran out and resume at the halted neuron
+    const int hn = g.halted_at;
+    int hl = 0;
+    while (hl + 1 < L && hn >= net.off[hl + 1]) ++hl;
+    long long V = c->Vcap, E = c->Ecap, T = c->Tcap;
+    if (g.halt_reason & (kHaltV | kHaltTape)) V = std::max(2 * V, (long long)(g.need_v * 1.3) + 1024);
+    if (g.halt_reason & kHaltE) E = std::max(2 * E, (long long)(g.need_e * 1.3) + 1024);
+    if (g.halt_reason & kHaltT) T = std::max(2 * T, pow2_at_least(g.need_t));
+    V = std::min<long long>(V, (1ll << 31) - 1);
+    E = std::min<long long>(E, (1ll << 31) - 1);
+    realloc_state(c, V, E, T, true);
+    // the neuron's counters restart from zero; the previous neuron used no table
+    PC_CUDA(cudaMemsetAsync(static_cast<Counters*>(c->cnt) + hn + 1, 0, sizeof(Counters), c->stream));
+    PC_CUDA(cudaMemsetAsync(&static_cast<Counters*>(c->cnt)[hn].tsize, 0, sizeof(long long), c->stream));
+    Global g0{};
+    g0.halted_at = -1;
+    g0.error = g.error;
+    *static_cast<Global*>(c->h_g) = g0;
+    PC_CUDA(cudaMemcpyAsync(c->g, c->h_g, sizeof(Global), cudaMemcpyHostToDevice, c->stream));
+    l0 = hl;
+    i0 = hn - net.off[hl];
+    gemm_done = true;
+    c->grows += 1;
+  }
+  PC_CUDA(cudaMemcpyAsync(c->h_cnt, c->cnt, sizeof(Counters) * (n + 1), cudaMemcpyDeviceToHost, c->stream));
+  PC_CUDA(cudaStreamSynchronize(c->stream));
+  const Counters* hc = static_cast<const Counters*>(c->h_cnt);
+  const Counters& last = hc[n];
+  c->nV = last.nV_before + last.nsplit;
+  c->nE = last.nE_before + last.nsplit + last.npairs;
+  c->have_result = true;
+  const Global g = *static_cast<Global*>(c->h_g);
+  long long degenerate = 0, undecided = 0;
+  bool pairing = (g.error & (kErrPairing | kErrProbe)) != 0;
+  for (int k = 1; k <= n; ++k) {
+    degenerate += hc[k].ndegenerate;
+    undecided += hc[k].nundecided;
+    if (hc[k].nkeys != 2 * hc[k].npairs) pairing = true;
+  }
+  c->degenerate = degenerate;
+  c->undecided = undecided;
+  if (pairing) throw PcError(PC_ERR_PAIRING, "a splitting 2-face did not occur exactly twice (non-generic input)");
+  if (g.error & kErrConflict) throw PcError(PC_ERR_PAIRING, "edge endpoints disagree on a processed sign entry");
+  if (c->opt.strict && (degenerate || undecided))
+    throw PcError(PC_ERR_DEGENERATE, "genericity violated: " + std::to_string(degenerate) + " exact zeros, " +
+                                          std::to_string(undecided) + " FP64-undecidable signs");
+}
+
+void StateBufs::release(pc_ctx* c) {
+  ctx_free(c, X);
+  ctx_free(c, Z[0]);
+  ctx_free(c, Z[1]);
+  ctx_free(c, esc);
+  ctx_free(c, SIG);
+  ctx_free(c, E);
+  ctx_free(c, stage);
+  ctx_free(c, table);
+  ctx_free(c, tape_pq);
+  ctx_free(c, tape_t);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+void pc_default_options(pc_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = PC_PREC_MIXED;
+  o->exec = PC_EXEC_PERSISTENT;
+  o->filter_kappa = 2.0;
+}
+
+pc_status pc_create(pc_ctx** out, int device, const pc_options* opt) {
+  if (!out) return PC_ERR_INVALID;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return PC_ERR_CUDA;
+  }
+  pc_ctx* c = new pc_ctx();
+  c->device = device;
+  pc_default_options(&c->opt);
+  if (opt) c->opt = *opt;
+  if (c->opt.precision < 0 || c->opt.precision > 2 || c->opt.exec < 0 || c->opt.exec > 1) {
+    delete c;
+    return PC_ERR_INVALID;
+  }
+  cudaSetDevice(device);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  *out = c;
+  return PC_OK;
+}
+
+pc_status pc_destroy(pc_ctx* c) {
+  if (!c) return PC_OK;
+  cudaSetDevice(c->device);
+  c->bufs.release(c);
+  ctx_free(c, c->params64);
+  ctx_free(c, c->params32);
+  ctx_free(c, c->norms);
+  ctx_free(c, c->cnt);
+  ctx_free(c, c->g);
+  ctx_free(c, c->cta);
+  c->release_extra();
+  cudaStreamSynchronize(c->stream);
+  if (c->h_cnt) cudaFreeHost(c->h_cnt);
+  if (c->h_g) cudaFreeHost(c->h_g);
+  delete c;
+  return PC_OK;
+}
+
+pc_status pc_set_allocator(pc_ctx* c, pc_alloc_fn a, pc_free_fn f, void* user) {
+  if (!c || (!a) != (!f)) return PC_ERR_INVALID;
+  if (c->allocated) return c->fail(PC_ERR_INVALID, "set the allocator before the first extraction");
+  c->alloc_fn = a;
+  c->free_fn = f;
+  c->alloc_user = user;
+  return PC_OK;
+}
+
+pc_status pc_extract(pc_ctx* c, int L, const int32_t* widths, const double* params, const double* lo,
+                     const double* hi, void* stream) {
+  if (!c || !widths || !params || !lo || !hi) return PC_ERR_INVALID;
+  c->err.clear();
+  c->have_result = false;
+  try {
+    PC_CUDA(cudaSetDevice(c->device));
+    c->stream = static_cast<cudaStream_t>(stream);
+    run_extract(c, L, widths, params, lo, hi);
+    return PC_OK;
+  } catch (const PcError& e) {
+    cudaGetLastError();
+    cudaStreamSynchronize(c->stream);
+    c->have_result = false;
+    return c->fail(e.status, e.what());
+  } catch (const std::exception& e) {
+    c->have_result = false;
+    return c->fail(PC_ERR_INVALID, e.what());
+  }
+}
+
+pc_status pc_counts(pc_ctx* c, int64_t* nv, int64_t* ne, int32_t* sw, int32_t* dim, int32_t* nent) {
+  if (!c) return PC_ERR_INVALID;
+  if (!c->have_result) return c->fail(PC_ERR_INVALID, "no extraction result");
+  if (nv) *nv = c->nV;
+  if (ne) *ne = c->nE;
+  if (sw) *sw = c->net.S;
+  if (dim) *dim = c->net.D;
+  if (nent) *nent = c->net.P;
+  return PC_OK;
+}
+
+static pc_status copy_rows(pc_ctx* c, void* out, const void* src, size_t elt, long long ld, long long n, int rows) {
+  if (!out || n == 0 || rows == 0) return PC_OK;
+  cudaError_t e = cudaMemcpy2DAsync(out, elt * n, src, elt * ld, elt * n, rows, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return c->fail(PC_ERR_CUDA, cudaGetErrorString(e));
+  return PC_OK;
+}
+
+pc_status pc_vertices(pc_ctx* c, const double** dev, int64_t* ld, double* out) {
+  if (!c) return PC_ERR_INVALID;
+  if (!c->have_result) return c->fail(PC_ERR_INVALID, "no extraction result");
+  if (dev) *dev = static_cast<const double*>(c->bufs.X);
+  if (ld) *ld = c->Vcap;
+  return copy_rows(c, out, c->bufs.X, 8, c->Vcap, c->nV, c->net.D);
+}
+
+pc_status pc_edges(pc_ctx* c, const int32_t** dev, int64_t* ld, int32_t* out) {
+  if (!c) return PC_ERR_INVALID;
+  if (!c->have_result) return c->fail(PC_ERR_INVALID, "no extraction result");
+  if (dev) *dev = static_cast<const int32_t*>(c->bufs.E);
+  if (ld) *ld = c->Ecap;
+  return copy_rows(c, out, c->bufs.E, 4, c->Ecap, c->nE, 2);
+}
+
+pc_status pc_signvectors(pc_ctx* c, const uint64_t** dev, int64_t* ld, uint64_t* out) {
+  if (!c) return PC_ERR_INVALID;
+  if (!c->have_result) return c->fail(PC_ERR_INVALID, "no extraction result");
+  if (dev) *dev = static_cast<const uint64_t*>(c->bufs.SIG);
+  if (ld) *ld = c->Vcap;
+  return copy_rows(c, out, c->bufs.SIG, 8, c->Vcap, c->nV, c->net.S);
+}
+
+pc_status pc_stats(pc_ctx* c, int64_t* out, int n_neurons) {
+  if (!c || !out) return PC_ERR_INVALID;
+  if (!c->have_result) return c->fail(PC_ERR_INVALID, "no extraction result");
+  if (n_neurons != c->N) return c->fail(PC_ERR_INVALID, "n_neurons does not match the last network");
+  const Counters* hc = static_cast<const Counters*>(c->h_cnt);
+  for (int k = 0; k < n_neurons; ++k) {
+    const Counters& s = hc[k + 1];
+    int64_t* o = out + 8 * k;
+    o[0] = s.nV_before; o[1] = s.nE_before; o[2] = s.nsplit; o[3] = s.nkeys;
+    o[4] = s.npairs; o[5] = s.nfilter; o[6] = s.nundecided; o[7] = s.ndegenerate;
+  }
+  return PC_OK;
+}
+
+const char* pc_last_error(pc_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// Host-side context of libpc (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <stdexcept>
+#include <string>
+#include <unordered_map>
+
+#include "pc.h"
+#include "pc_device.cuh"
+
+struct pc_ctx;
+
+void* ctx_alloc(pc_ctx* c, size_t bytes);
+void ctx_free(pc_ctx* c, void*& p);
+
+struct PcError : std::runtime_error {
+  pc_status status;
+  PcError(pc_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+struct StateBufs {
+  void* X = nullptr;
+  void* Z[2] = {nullptr, nullptr};
+  void* esc = nullptr;
+  void* SIG = nullptr;
+  void* E = nullptr;
+  void* stage = nullptr;
+  void* table = nullptr;
+  void* tape_pq = nullptr;
+  void* tape_t = nullptr;
+  void release(pc_ctx* c);
+};
+
+struct pc_ctx {
+  int device = 0;
+  int num_sms = 1;
+  pc_options opt{};
+  std::string err;
+  cudaStream_t stream = nullptr;
+  pc_alloc_fn alloc_fn = nullptr;
+  pc_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  size_t allocated = 0;
+  std::unordered_map<void*, size_t> sizes;
+
+  // network of the last extraction
+  pc::NetDesc net{};
+  int hmax = 0, mw = 0, N = 0;
+  void* params64 = nullptr;
+  void* params32 = nullptr;
+  void* norms = nullptr;
+  long long params_cap = 0;
+
+  // state
+  StateBufs bufs;
+  long long Vcap = 0, Ecap = 0, Tcap = 0;
+  int shape_D = 0, shape_S = 0, shape_H = 0, shape_tape = -1;
+  size_t shape_zs = 0;
+  void* cnt = nullptr;
+  int cnt_slots = 0;
+  void* g = nullptr;
+  void* cta = nullptr;
+  void* h_cnt = nullptr;
+  void* h_g = nullptr;
+
+  // launch geometry
+  int grid_persist = 0, grid_step = 0, res_warps = 1;
+  size_t res_smem = 0;
+
+  // results
+  long long nV = 0, nE = 0;
+  long long degenerate = 0, undecided = 0;
+  long long grows = 0;
+  bool have_result = false;
+
+  // adjoint scratch (allocated lazily by pc_backward)
+  void* adj[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t adj_bytes[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+
+  pc_status fail(pc_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+  void release_extra() {
+    for (auto& p : adj) ctx_free(this, p);
+  }
+};

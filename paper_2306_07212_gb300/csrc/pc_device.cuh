@@ -1,0 +1,168 @@
+// Device-side data structures and helpers of the edge-subdivision engine.
+//
+// State layout in HBM (structure of arrays, leading dimension = capacity):
+//   X     [D][Vcap]   float64 vertex coordinates
+//   Z     [H][Vcap]   current-layer pre-activations (float32, or float64 in
+//                     FP64 mode), neuron-major so one neuron's pass reads a
+//                     contiguous row; two buffers ping-pong across layers
+//   esc   [Vcap]      float32 absolute error bound of the vertex's Z column
+//                     (mixed precision only)
+//   SIG   [S][Vcap]   packed sign vectors, 2 bits per entry, word-major
+//   EU/EW [Ecap]      int32 edge endpoints (EW = EU + Ecap)
+//   stage [Ecap]      splitting-edge ids, staged per CTA range
+//   table [Tcap]      open-addressing hash table of 2-face keys
+//   cnt   [N+1]       per-neuron counters (slot n+1 belongs to neuron n)
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pc {
+
+constexpr int kMaxD = 8;
+constexpr int kMaxL = 16;
+constexpr int kMaxWidth = 256;
+constexpr int kMaxEntries = 1024;
+constexpr int kMaxWords = kMaxEntries / 32;
+
+constexpr uint64_t kPlus = 1;   // code 01
+constexpr uint64_t kMinus = 2;  // code 10
+constexpr uint64_t kEvenBits = 0x5555555555555555ull;
+
+constexpr uint64_t kEmpty = ~0ull;       // empty hash slot
+constexpr uint64_t kPaired = 1ull << 31; // payload flag: face already paired
+
+constexpr int kBlock = 512;              // threads per CTA in the neuron phases
+constexpr int kWarps = kBlock / 32;
+constexpr int kMaxGrid = 2048;           // upper bound on CTAs of a phase grid
+constexpr int kFilterCap = 2 * kBlock;   // CTA-local list of filtered vertices
+
+// error bits in Global::error
+constexpr int kErrPairing = 1;
+constexpr int kErrDegenerate = 2;
+constexpr int kErrTimeout = 4;
+constexpr int kErrProbe = 8;
+constexpr int kErrConflict = 16;
+
+// halt reasons
+constexpr int kHaltV = 1, kHaltE = 2, kHaltT = 4, kHaltTape = 8;
+
+struct NetDesc {
+  int L, D, m, N, P, S;
+  int precision;         // pc_precision
+  int w[kMaxL + 1];      // widths
+  int off[kMaxL + 1];    // global index of the first neuron of layer l
+  long long wofs[kMaxL]; // offset of W_l in the flat parameter array
+  long long bofs[kMaxL]; // offset of b_l
+  double lo[kMaxD], hi[kMaxD];
+  const double* W64;     // flat parameters, float64 (device copy)
+  const float* W32;      // flat parameters rounded to float32
+  const float* norms;    // per layer: [2l] = max_j sum_k |W_jk|, [2l+1] = max_j |b_j|
+  float kappa;           // filter factor
+};
+
+struct Counters {        // 128 bytes
+  long long nV_before, nE_before;
+  long long nsplit, nkeys, npairs;
+  long long nfilter, nundecided, ndegenerate;
+  long long tsize;
+  long long pad[7];
+};
+
+struct Global {
+  int halted_at;         // -1, or the neuron whose step ran out of capacity
+  int halt_reason;
+  int error;             // sticky kErr* bits
+  int pad0;
+  unsigned int barrier;  // grid barrier arrival counter (reset per launch)
+  unsigned int pad1;
+  long long need_v, need_e, need_t;
+  long long pad[3];
+};
+
+struct State {
+  long long Vcap, Ecap, Tcap;
+  double* X;
+  void* Z[2];
+  float* esc;
+  uint64_t* SIG;
+  int32_t* EU;
+  int32_t* EW;
+  int32_t* stage;
+  uint64_t* table;
+  Counters* cnt;
+  Global* g;
+  long long* cta_count;
+  // interpolation tape (optional): parents and t of every created vertex
+  int32_t* tape_pq;      // [2][tape_cap] indexed by vertex id
+  double* tape_t;        // [tape_cap]
+  long long tape_cap;
+  int keep_tape;
+};
+
+// splitmix64 finalizer (Steele, Lea, Flood 2014) as the per-word mixer of the
+// 2-face fingerprint.
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  x ^= x >> 31;
+  return x;
+}
+
+__device__ __forceinline__ uint64_t word_hash(int w, uint64_t v) {
+  return mix64(v ^ (0x9e3779b97f4a7c15ull * (uint64_t)(w + 1)));
+}
+
+// Bit 2r is set iff entry 32w + r is valid (< n_valid) and has code 00.
+__device__ __forceinline__ uint64_t zero_mask(uint64_t s, int w, int n_valid) {
+  const int cnt = n_valid - 32 * w;
+  if (cnt <= 0) return 0;
+  const uint64_t valid = cnt >= 32 ? kEvenBits : (((1ull << (2 * cnt)) - 1) & kEvenBits);
+  const uint64_t nz = (s | (s >> 1)) & kEvenBits;
+  return ~nz & valid;
+}
+
+__device__ __forceinline__ uint64_t code_at(const uint64_t* SIG, long long Vcap, long long v, int entry) {
+  return (SIG[(long long)(entry >> 5) * Vcap + v] >> (2 * (entry & 31))) & 3ull;
+}
+
+__device__ __forceinline__ long long atomic_add_ll(long long* p, long long x) {
+  return (long long)atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)x);
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier for cooperative launches.  Bounded: after ~0.5 s of
+// waiting it sets kErrTimeout and returns false (the caller then exits).
+__device__ __forceinline__ bool grid_barrier(Global* g, unsigned int& passed) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    passed += 1;
+    const unsigned int target = passed * gridDim.x;
+    __threadfence();
+    atomicAdd(&g->barrier, 1u);
+    int ok = 1;
+    long long spins = 0;
+    while (ld_acquire_u32(&g->barrier) < target) {
+      if (++spins > (1ll << 22)) {
+        atomicOr(&g->error, kErrTimeout);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+}  // namespace pc

@@ -1,0 +1,125 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Sign vectors and edge sets must be bit-identical after canonical ordering;
+coordinates within 1e-6 of the box diameter (2*sqrt(D) for [-1,1]^D).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_07212_gb300 import workloads as wl
+from _util import assert_same_complex, canon, unpack_codes, entry_values
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_triple(ex):
+    c = ex.counts()
+    return ex.vertices(), unpack_codes(ex.sign_words(), c["P"]), ex.edges()
+
+
+def _tol(box):
+    return 1e-6 * float(np.linalg.norm(box.hi - box.lo))
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2306_07212_gb300 import Extractor
+    return Extractor
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("execution", ["persistent", "stepwise"])
+def test_small_d2_config(cuda, precision, execution):
+    net, box = wl.small_d2()
+    ref = oracle.extract(net, box)
+    with cuda(precision=precision, execution=execution) as ex:
+        ex.extract(net, box)
+        assert_same_complex(_gpu_triple(ex), (ref.X, ref.S, ref.E), coord_tol=_tol(box),
+                            what=f"2-8-8-1 {precision} {execution}")
+        st = ex.stats()
+        assert np.array_equal(st[:, 2], ref.stats[:, 0]), "splits per neuron"
+        assert np.array_equal(st[:, 4], ref.stats[:, 2]), "paired faces per neuron"
+
+
+SWEEP = [(1, [1, 8, 8, 1]), (1, [1, 16, 16, 16, 1]), (2, [2, 4, 1]), (2, [2, 16, 16, 1]),
+         (2, [2, 12, 12, 12, 12, 1]), (3, [3, 8, 8, 1]), (3, [3, 16, 16, 1]), (3, [3, 6, 6, 6, 6, 2]),
+         (4, [4, 8, 8, 1]), (4, [4, 12, 12, 1]), (2, [2, 40, 1]), (3, [3, 2, 2, 1])]
+
+
+@pytest.mark.parametrize("D,widths", SWEEP)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_random_sweep(cuda, D, widths, precision):
+    for seed in range(3):
+        net = wl.he_normal_mlp(widths, seed=1000 + seed)
+        box = wl.Box.cube(D)
+        ref = oracle.extract(net, box)
+        assert ref.status == 0
+        with cuda(precision=precision) as ex:
+            ex.extract(net, box)
+            assert_same_complex(_gpu_triple(ex), (ref.X, ref.S, ref.E), coord_tol=_tol(box),
+                                what=f"{widths} seed {seed} {precision}")
+
+
+@pytest.mark.parametrize("execution", ["persistent", "stepwise"])
+def test_capacity_growth_replays_to_same_result(cuda, execution):
+    net = wl.he_normal_mlp([3, 16, 16, 16, 1], seed=4)
+    box = wl.Box.cube(3)
+    ref = oracle.extract(net, box)
+    with cuda(precision="mixed", execution=execution, init_vcap=64, init_ecap=64) as ex:
+        ex.extract(net, box)
+        assert_same_complex(_gpu_triple(ex), (ref.X, ref.S, ref.E), coord_tol=_tol(box), what="growth")
+    with cuda(precision="mixed", execution=execution) as ex:
+        ex.extract(net, box)
+        assert_same_complex(_gpu_triple(ex), (ref.X, ref.S, ref.E), coord_tol=_tol(box), what="no growth")
+
+
+def test_context_reuse_across_networks(cuda):
+    nets = [wl.he_normal_mlp(w, seed=s) for s, w in enumerate([[2, 8, 1], [3, 16, 16, 1], [2, 8, 8, 8, 1]])]
+    with cuda(precision="mixed") as ex:
+        for net in nets + nets[::-1]:
+            box = wl.Box.cube(net.D)
+            ref = oracle.extract(net, box)
+            ex.extract(net, box)
+            assert_same_complex(_gpu_triple(ex), (ref.X, ref.S, ref.E), coord_tol=_tol(box), what="reuse")
+
+
+def test_diff_config_d3(cuda):
+    net, box = wl.diff_d3()
+    ref = oracle.extract(net, box)
+    with cuda(precision="mixed") as ex:
+        ex.extract(net, box)
+        assert_same_complex(_gpu_triple(ex), (ref.X, ref.S, ref.E), coord_tol=_tol(box), what="3-32-32-32-1")
+
+
+def test_torus_config_full_size(cuda):
+    """The D=3 torus network at full size (~3e5 vertices, ~9e5 edges)."""
+    net, box = wl.torus_d3()
+    ref = oracle.extract(net, box)
+    assert ref.status == 0
+    with cuda(precision="mixed") as ex:
+        ex.extract(net, box)
+        got = _gpu_triple(ex)
+        assert_same_complex(got, (ref.X, ref.S, ref.E), coord_tol=_tol(box), what="torus")
+        # the paper's validation (Section 5.1.1): zero entries evaluate to ~0
+        vals = entry_values(net, box, got[0])
+        assert np.max(np.abs(vals[got[1] == 0])) < 1e-6
+
+
+def test_zero_residual_and_degree_any_size(cuda):
+    """Properties that hold at any size, checked on a larger D=4 net."""
+    net = wl.he_normal_mlp([4, 24, 24, 1], seed=3)
+    box = wl.Box.cube(4)
+    with cuda(precision="mixed") as ex:
+        ex.extract(net, box)
+        X, S, E = _gpu_triple(ex)
+    D, m = 4, 8
+    assert np.all((S == 0).sum(axis=1) == D)
+    deg = np.bincount(E.ravel(), minlength=len(X))
+    assert np.array_equal(deg, 2 * D - (S[:, :m] == 0).sum(axis=1))
+    vals = entry_values(net, box, X)
+    assert np.max(np.abs(vals[S == 0])) < 1e-6
+    assert np.all(np.sign(vals[S != 0]) == S[S != 0])
