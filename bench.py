@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""Benchmark: vertices+edges per second of edge-subdivision extraction.
+
+Workload: the D=3 torus network (3-64-64-64-64-1, fitted to a torus SDF) on the
+box [-1,1]^3, mixed precision (FP32 values, FP64 coordinates / t / filtered
+sign predicates), one full extraction per step.  Inputs (the network
+parameters) are resident in device memory when the timed region starts; the
+L2 cache is flushed (a 512 MiB write) before every step, outside the step's
+CUDA events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build)
+on the host cores.  Under torchrun (N > 1) every rank runs an independent
+replica on its own GPU (the extraction does not shard); rank 0 prints one JSON
+line with the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vertices+edges/s at D=3 (torus 3-64x4-1, box [-1,1]^3)"
+UNIT = "(V+E)/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _workload():
+    from paper_2306_07212_gb300 import workloads
+    net, box = workloads.torus_d3()
+    return net, box, {"workload": "torus SDF net D=3, MLP 3-64x4-1, box [-1,1]^3, one full extraction per step"}
+
+
+# -- clocks -------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "0x1") or val == "Active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -- algorithmic bytes of the neuron loop -------------------------------------
+
+def neuron_loop_bytes(net, stats, precision: str) -> list:
+    """Bytes the per-neuron steps must move, per layer (one persistent launch each).
+
+    Per neuron step with V vertices, E edges, S splitting edges, K keys, P pairs:
+      sign   : V * (zb + 16)              z row read, sign word read+write
+      edges  : E * 8 + S * 4              endpoints read, splitting ids written
+      split  : S * (3 * (8D + H zb + 8W) + 28)   two endpoint records read, one
+               new record written (coordinates, H values, W sign words), split
+               id read, edge read and two edge writes
+      pairing: K * 16 + P * 8             hash slot write+read, new edge write
+    zb = 4 (FP32 values) or 8 (FP64); W = 64-bit words per sign vector.
+    """
+    D = net.D
+    zb = 8 if precision == "fp64" else 4
+    W = (2 * D + net.n_neurons + 31) // 32
+    out, n = [], 0
+    for l in range(net.L):
+        H = net.widths[l + 1]
+        tot = 0
+        for _ in range(H):
+            V, E, S, K, P = (int(stats[n, k]) for k in (0, 1, 2, 3, 4))
+            tot += V * (zb + 16) + E * 8 + S * 4 + S * (3 * (8 * D + H * zb + 8 * W) + 28) + K * 16 + P * 8
+            n += 1
+        out.append(tot)
+    return out
+
+
+# -- our arm -------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2306_07212_gb300 import Extractor
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    net, box, config = _workload()
+    dev = torch.device("cuda", local_rank)
+    params_dev = torch.from_numpy(net.flat_params()).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ex = Extractor(device=local_rank, precision=args.precision, execution=args.execution, timers=True)
+    for _ in range(args.warmup):
+        ex.extract(net, box, params=params_dev)
+    c = ex.counts()
+    units = c["nV"] + c["nE"]
+    stats = ex.stats()
+    layer_bytes = neuron_loop_bytes(net, stats, args.precision)
+    launches0 = ex.diagnostics()["launches"]
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, loop_ms, gemm_ms = [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ex.extract(net, box, params=params_dev)
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kt = ex.kernel_times_ms()
+        loop_ms.append(kt[:, 1].copy())
+        gemm_ms.append(kt[:, 0].copy())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = ex.diagnostics()["launches"] - launches0
+    assert ex.counts()["nV"] + ex.counts()["nE"] == units
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+
+    # end to end through the C ABI with host buffers: parameters from pinned
+    # host memory each step, the complex copied back to pinned host memory
+    params_host = torch.from_numpy(net.flat_params()).pin_memory()
+    S = c["S"]
+    Xh = torch.empty((c["D"], c["nV"]), dtype=torch.float64).pin_memory()
+    Eh = torch.empty((2, c["nE"]), dtype=torch.int32).pin_memory()
+    Sh = torch.empty((S, c["nV"]), dtype=torch.int64).pin_memory()
+    lib, ctx = ex._lib, ex._ctx
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ex.extract(net, box, params=params_host)
+        ex._check(lib.pc_vertices(ctx, None, None, Xh.data_ptr()))
+        ex._check(lib.pc_edges(ctx, None, None, Eh.data_ptr()))
+        ex._check(lib.pc_signvectors(ctx, None, None, Sh.data_ptr()))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = params_host.numel() * 8
+    d2h = Xh.numel() * 8 + Eh.numel() * 4 + Sh.numel() * 8
+
+    loop_avg = np.mean(np.stack(loop_ms), axis=0)  # per layer, ms
+    gemm_avg = np.mean(np.stack(gemm_ms), axis=0)
+    peak, peak_kind = _peaks()
+    achieved = sum(layer_bytes) / (loop_avg.sum() / 1e3) / 1e9
+    roofline = {"kernel": "k_layer (persistent neuron loop, one launch per layer)", "bound": "hbm",
+                "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind, "traffic": None,
+                "bytes_per_launch_avg": int(sum(layer_bytes) / len(layer_bytes)),
+                "launch_ms_avg": round(float(loop_avg.mean()), 4),
+                "share_of_step": round(float(loop_avg.sum() / statistics.mean(step_ms)), 3),
+                "forward_product_ms_per_step": round(float(gemm_avg.sum()), 4)}
+    out = None
+    if rank == 0:
+        cpu = cpu_baseline(net, box) if world == 1 else None
+        value = units * args.steps * world / total_s
+        out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": round(total_s * 1e3 / args.steps, 4), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else
+               {"fp32": "f32", "fp64": "f64"}[args.precision],
+               "data": "synthetic (torus SDF net fitted from seed 0)",
+               "config": dict(config, precision=args.precision, execution=args.execution, n_vertices=c["nV"],
+                              n_edges=c["nE"], l2="flushed by a 512 MiB write before every step",
+                              parallelism="replicas" if world > 1 else "single GPU"),
+               "e2e": {"value": round(units * args.steps * world / e2e_s, 1), "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+               "gpu_launches": int(launches), "roofline": roofline, "clocks": clk,
+               "step_ms_median": round(statistics.median(step_ms), 4)}
+        if cpu:
+            out["cpu_baseline"] = cpu
+    ex.close()
+    if dist:
+        dist.destroy_process_group()
+    return out
+
+
+def cpu_baseline(net, box):
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.extract(net, box)
+    dt = time.perf_counter() - t0
+    return {"value": round((r.nV + r.nE) / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full FP64 oracle extraction of the same workload ({r.nV} V, {r.nE} E) in {dt:.2f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    net, box, config = _workload()
+    for _ in range(args.warmup):
+        oracle.extract(net, box)
+    times = []
+    units = 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.extract(net, box)
+        times.append(time.perf_counter() - t0)
+        units = r.nV + r.nE
+    total = sum(times)
+    value = units * args.steps / total
+    cpu = {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"full FP64 oracle extraction of the workload per step ({units} V+E)"}
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / args.steps, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (torus SDF net fitted from seed 0)", "config": dict(config, precision="fp64"),
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
+    ap.add_argument("--execution", default="persistent", choices=["persistent", "stepwise"])
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local_rank)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

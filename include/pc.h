@@ -77,10 +77,17 @@ typedef struct {
   int64_t init_vcap;      /* initial vertex capacity (grown x2 on overflow) */
   int64_t init_ecap;      /* initial edge capacity */
   int64_t mem_budget_bytes; /* 0 = no limit */
-  double filter_kappa;    /* PC_PREC_MIXED: re-evaluate when |z| <= kappa * bound */
+  double filter_kappa;    /* PC_PREC_MIXED: re-evaluate a sign in FP64 when
+                             |z| <= kappa * (FP32 error estimate of z) */
+  int polish;             /* FP64 Newton polish of vertices whose coordinate
+                             error estimate exceeds polish_tol * box diameter:
+                             1 on, 0 off, -1 on in PC_PREC_MIXED only */
+  double polish_tol;      /* relative to the box diameter (default 1e-7) */
+  int timers;             /* record CUDA events around each layer's kernels */
 } pc_options;
 
-/* Fills *opt with defaults (mixed precision, persistent execution). */
+/* Fills *opt with defaults (mixed precision, persistent execution,
+ * filter_kappa 4, polish in mixed precision with polish_tol 1e-7). */
 void pc_default_options(pc_options *opt);
 
 /* Creates a context on CUDA device `device`.  opt may be NULL (defaults). */
@@ -133,6 +140,17 @@ pc_status pc_stats(pc_ctx *ctx, int64_t *out, int n_neurons);
  * grad_params: flat float64 array in the parameter layout, host or device;
  * overwritten.  Needs keep_tape = 1 at extraction (else PC_ERR_NO_TAPE). */
 pc_status pc_backward(pc_ctx *ctx, const double *grad_x, double *grad_params, void *stream);
+
+/* Diagnostics of the last extraction, up to n int64 values: kernel launches
+ * (cumulative over the context's life), capacity growths, polished vertices,
+ * exact-zero pre-activations, FP64-undecidable signs, vertex / edge / hash
+ * capacities, device bytes held, CTAs of the persistent kernel. */
+pc_status pc_diagnostics(pc_ctx *ctx, int64_t *out, int n);
+
+/* With opt.timers: device time in ms of the last extraction's kernels per
+ * layer, out_ms[2l] = layer-start forward product, out_ms[2l+1] = the neuron
+ * loop of layer l (-1 where not measured). */
+pc_status pc_kernel_times(pc_ctx *ctx, double *out_ms, int n);
 
 /* Message of the last error on this context ("" if none). */
 const char *pc_last_error(pc_ctx *ctx);

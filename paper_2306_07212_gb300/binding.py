@@ -26,7 +26,7 @@ EXEC = {"persistent": 0, "stepwise": 1}
 # Every symbol include/pc.h declares (checked by the tests).
 EXPORTS = ["pc_default_options", "pc_create", "pc_destroy", "pc_set_allocator", "pc_extract",
            "pc_counts", "pc_vertices", "pc_edges", "pc_signvectors", "pc_stats", "pc_backward",
-           "pc_last_error"]
+           "pc_diagnostics", "pc_kernel_times", "pc_last_error"]
 
 
 class PcError(RuntimeError):
@@ -38,7 +38,8 @@ class PcError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("exec", ctypes.c_int), ("keep_tape", ctypes.c_int),
                 ("strict", ctypes.c_int), ("init_vcap", ctypes.c_int64), ("init_ecap", ctypes.c_int64),
-                ("mem_budget_bytes", ctypes.c_int64), ("filter_kappa", ctypes.c_double)]
+                ("mem_budget_bytes", ctypes.c_int64), ("filter_kappa", ctypes.c_double),
+                ("polish", ctypes.c_int), ("polish_tol", ctypes.c_double), ("timers", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -71,6 +72,8 @@ def load_library(path: str = LIB):
         lib.pc_signvectors.argtypes = [vp, ctypes.POINTER(vp), i64p, vp]
         lib.pc_stats.argtypes = [vp, i64p, ctypes.c_int]
         lib.pc_backward.argtypes = [vp, vp, vp, vp]
+        lib.pc_diagnostics.argtypes = [vp, i64p, ctypes.c_int]
+        lib.pc_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         lib.pc_last_error.argtypes = [vp]
         lib.pc_last_error.restype = ctypes.c_char_p
         for f in EXPORTS:
@@ -108,7 +111,8 @@ class Extractor:
 
     def __init__(self, device: int = 0, precision: str = "mixed", execution: str = "persistent",
                  keep_tape: bool = False, strict: bool = False, init_vcap: int = 0, init_ecap: int = 0,
-                 mem_budget_bytes: int = 0, kappa: float = 2.0, torch_allocator: bool = True):
+                 mem_budget_bytes: int = 0, kappa: float = 4.0, polish: int = -1, polish_tol: float = 1e-7,
+                 timers: bool = False, torch_allocator: bool = True):
         self._lib = load_library()
         o = Options()
         self._lib.pc_default_options(ctypes.byref(o))
@@ -119,6 +123,9 @@ class Extractor:
         o.init_vcap, o.init_ecap = int(init_vcap), int(init_ecap)
         o.mem_budget_bytes = int(mem_budget_bytes)
         o.filter_kappa = float(kappa)
+        o.polish = int(polish)
+        o.polish_tol = float(polish_tol)
+        o.timers = int(timers)
         self.device = device
         self.options = o
         self._ctx = ctypes.c_void_p()
@@ -215,6 +222,20 @@ class Extractor:
         out = np.zeros((N, 8), np.int64)
         self._check(self._lib.pc_stats(self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), N))
         return out
+
+    def diagnostics(self) -> dict:
+        out = np.zeros(10, np.int64)
+        self._check(self._lib.pc_diagnostics(self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 10))
+        keys = ["launches", "grows", "polished", "degenerate", "undecided", "vcap", "ecap", "tcap",
+                "bytes", "persistent_ctas"]
+        return dict(zip(keys, (int(x) for x in out)))
+
+    def kernel_times_ms(self) -> np.ndarray:
+        """(L, 2) ms per layer: forward product, neuron loop (-1: not measured)."""
+        L = len(self.net.widths) - 1
+        out = np.full(2 * L, -1.0)
+        self._check(self._lib.pc_kernel_times(self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 2 * L))
+        return out.reshape(L, 2)
 
     def device_arrays(self):
         """(X ptr, ld), (E ptr, ld), (SIG ptr, ld) of the context's device buffers."""

@@ -20,7 +20,7 @@ namespace pc {
 // Set-up kernels
 
 // float32 copy of the parameters and per-layer norms used by the FP32 error
-// bound: max_j sum_k |W_jk| and max_j |b_j| (rounded up).
+// estimate: max_j ||W_j||_2 and max_j |b_j| (rounded up).
 __global__ void k_prep(NetDesc net, float* W32, float* norms, long long n_params) {
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n_params;
        t += (long long)gridDim.x * blockDim.x)
@@ -31,8 +31,11 @@ __global__ void k_prep(NetDesc net, float* W32, float* norms, long long n_params
     double mw = 0.0, mb = 0.0;
     for (int j = threadIdx.x; j < H; j += blockDim.x) {
       double s = 0.0;
-      for (int k = 0; k < K; ++k) s += fabs(net.W64[net.wofs[l] + (long long)j * K + k]);
-      mw = fmax(mw, s);
+      for (int k = 0; k < K; ++k) {
+        const double w = net.W64[net.wofs[l] + (long long)j * K + k];
+        s += w * w;
+      }
+      mw = fmax(mw, sqrt(s));
       mb = fmax(mb, fabs(net.W64[net.bofs[l] + j]));
     }
     s_w[threadIdx.x] = mw;
@@ -64,6 +67,7 @@ __global__ void k_init(NetDesc net, State st) {
     }
     st.SIG[c] = w0;
     for (int w = 1; w < net.S; ++w) st.SIG[(long long)w * Vcap + c] = 0;
+    if (st.exc) st.exc[c] = 0.f;
   }
   for (int e = threadIdx.x; e < ne0; e += blockDim.x) {
     const int d = e >> (D - 1), r = e & ((1 << (D - 1)) - 1);
@@ -89,6 +93,7 @@ __global__ void k_init(NetDesc net, State st) {
 template <typename ZT, bool MIXED>
 __global__ void __launch_bounds__(128) k_gemm_simt(NetDesc net, State st, int l) {
   constexpr int TJ = 16;
+  constexpr bool TRACK = sizeof(ZT) == 4;
   if (st.g->halted_at >= 0 || (st.g->error & kErrTimeout)) return;
   const Counters* c = st.cnt + net.off[l];
   const long long nV = c->nV_before + c->nsplit;
@@ -152,10 +157,13 @@ __global__ void __launch_bounds__(128) k_gemm_simt(NetDesc net, State st, int l)
 #pragma unroll
     for (int jj = 0; jj < TJ; ++jj)
       if (j0 + jj < H) Zout[(long long)(j0 + jj) * Vcap + v] = acc[jj];
-    if (MIXED && blockIdx.y == 0) {
+    if (TRACK && blockIdx.y == 0) {
+      // Error estimate of the FP32 column (statistical, not a worst case):
+      // rounding ~ 2u (sqrt(K) + 2)(||W_j||_2 max|a| + |b|), plus the inputs'
+      // estimate propagated through ||W_j||_2.
       const float wn = net.norms[2 * l], bm = net.norms[2 * l + 1];
-      if (l == 0) st.esc[v] = 1.2e-7f * (wn * amax + bm);
-      else st.esc[v] = float(K + 4) * 1.2e-7f * (wn * amax + bm) + wn * st.esc[v];
+      const float rnd = 1.2e-7f * (sqrtf(float(K)) + 2.f) * (wn * amax + bm);
+      st.esc[v] = (l == 0) ? rnd : rnd + wn * st.esc[v];
     }
   }
 }
@@ -168,11 +176,11 @@ __device__ __forceinline__ bool stopped(const State& st) {
 }
 
 template <typename ZT, bool MIXED>
-__global__ void __launch_bounds__(kBlock) k_sign(NetDesc net, State st, int l, int i, int mw, int res_warps) {
+__global__ void __launch_bounds__(kBlock) k_sign(NetDesc net, State st, int l, int i, int mw) {
   extern __shared__ double dsm[];
   __shared__ Smem sm;
   if (stopped(st)) return;
-  phase_sign<ZT, MIXED>(net, st, l & 1, l, i, net.off[l] + i, sm, dsm, mw, res_warps);
+  phase_sign<ZT, MIXED>(net, st, l & 1, l, i, net.off[l] + i, sm, dsm, mw);
 }
 
 __global__ void __launch_bounds__(kBlock) k_edges(NetDesc net, State st, int l, int i) {
@@ -189,8 +197,7 @@ __global__ void __launch_bounds__(kBlock) k_split(NetDesc net, State st, int l, 
 }
 
 template <typename ZT, bool MIXED>
-__global__ void __launch_bounds__(kBlock) k_layer(NetDesc net, State st, int l, int i_begin, int mw,
-                                                   int res_warps) {
+__global__ void __launch_bounds__(kBlock) k_layer(NetDesc net, State st, int l, int i_begin, int mw) {
   extern __shared__ double dsm[];
   __shared__ Smem sm;
   if (stopped(st)) return;
@@ -198,13 +205,50 @@ __global__ void __launch_bounds__(kBlock) k_layer(NetDesc net, State st, int l, 
   const int H = net.w[l + 1];
   for (int i = i_begin; i < H; ++i) {
     const int n = net.off[l] + i;
-    phase_sign<ZT, MIXED>(net, st, l & 1, l, i, n, sm, dsm, mw, res_warps);
+    phase_sign<ZT, MIXED>(net, st, l & 1, l, i, n, sm, dsm, mw);
     if (!grid_barrier(st.g, passed)) return;
     phase_edges(net, st, n, sm);
     if (!grid_barrier(st.g, passed)) return;
     if (phase_split<ZT, MIXED>(net, st, l & 1, l, i, n, sm)) return;
     if (!grid_barrier(st.g, passed)) return;
   }
+}
+
+// Coordinate polish: every vertex whose coordinate error estimate exceeds
+// thr is moved to its exact position by an FP64 Newton step on its D zero
+// entries (all entries are processed at this point).
+__global__ void __launch_bounds__(kBlock) k_polish(NetDesc net, State st, float thr, int mw) {
+  extern __shared__ double dsm[];
+  __shared__ Smem sm;
+  if (stopped(st)) return;
+  const Counters* last = st.cnt + net.N;
+  const long long nV = last->nV_before + last->nsplit;
+  const long long Vcap = st.Vcap;
+  long long npol = 0;
+  if (threadIdx.x == 0) sm.fcount = 0;
+  __syncthreads();
+  for (long long base = (long long)blockIdx.x * kBlock; base < nV; base += (long long)gridDim.x * kBlock) {
+    const long long v = base + threadIdx.x;
+    if (v < nV && !(st.exc[v] <= thr)) {
+      const int slot = atomicAdd(&sm.fcount, 1);
+      sm.flist[slot] = v;
+    }
+    __syncthreads();
+    const int fc = sm.fcount;
+    for (int q = 0; q < fc; ++q) {
+      const long long u = sm.flist[q];
+      newton_cta(net, st, u, net.P, -1, -1, mw, dsm, sm.nzl, &sm.nout);
+      if (sm.nout.ok) {
+        if (threadIdx.x < net.D) st.X[(long long)threadIdx.x * Vcap + u] += sm.nout.dlt[threadIdx.x];
+        if (threadIdx.x == 0) st.exc[u] = 0.f;
+        npol += (threadIdx.x == 0);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sm.fcount = 0;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && npol) atomic_add_ll(&st.g->polished, npol);
 }
 
 }  // namespace pc
@@ -267,6 +311,7 @@ static void realloc_state(pc_ctx* c, long long V, long long E, long long T, bool
   A(nb.Z[0], zs * Hm * V);
   A(nb.Z[1], zs * Hm * V);
   A(nb.esc, sizeof(float) * V);
+  A(nb.exc, sizeof(float) * V);
   A(nb.SIG, sizeof(uint64_t) * S * V);
   A(nb.E, sizeof(int32_t) * 2 * E);
   A(nb.stage, sizeof(int32_t) * E);
@@ -286,6 +331,7 @@ static void realloc_state(pc_ctx* c, long long V, long long E, long long T, bool
     cp2(nb.Z[0], zs * V, ob.Z[0], zs * oV, zs * nV, Hm);
     cp2(nb.Z[1], zs * V, ob.Z[1], zs * oV, zs * nV, Hm);
     cp2(nb.esc, 4 * V, ob.esc, 4 * oV, 4 * nV, 1);
+    cp2(nb.exc, 4 * V, ob.exc, 4 * oV, 4 * nV, 1);
     cp2(nb.SIG, 8 * V, ob.SIG, 8 * oV, 8 * nV, S);
     cp2(nb.E, 4 * E, ob.E, 4 * oE, 4 * nE, 2);
     if (c->opt.keep_tape && ob.tape_pq) {
@@ -327,6 +373,7 @@ static State make_state(pc_ctx* c) {
   s.Z[0] = c->bufs.Z[0];
   s.Z[1] = c->bufs.Z[1];
   s.esc = static_cast<float*>(c->bufs.esc);
+  s.exc = static_cast<float*>(c->bufs.exc);
   s.SIG = static_cast<uint64_t*>(c->bufs.SIG);
   s.EU = static_cast<int32_t*>(c->bufs.E);
   s.EW = s.EU + c->Ecap;
@@ -342,30 +389,57 @@ static State make_state(pc_ctx* c) {
   return s;
 }
 
+// CUDA events around the kernels of one layer (index 2l: forward product,
+// 2l+1: neuron loop), recorded on the extraction's stream when timers are on.
+struct TimerScope {
+  pc_ctx* c;
+  int slot;
+  TimerScope(pc_ctx* c_, int s) : c(c_), slot(s) {
+    if (c->opt.timers && slot < 2 * kMaxL) {
+      if (!c->ev[slot][0]) {
+        cudaEventCreate(&c->ev[slot][0]);
+        cudaEventCreate(&c->ev[slot][1]);
+      }
+      cudaEventRecord(c->ev[slot][0], c->stream);
+    }
+  }
+  ~TimerScope() {
+    if (c->opt.timers && slot < 2 * kMaxL) {
+      cudaEventRecord(c->ev[slot][1], c->stream);
+      c->ev_used[slot] = 1;
+    }
+  }
+};
+
 template <typename ZT, bool MIXED>
 struct Kernels {
   static void gemm(pc_ctx* c, const State& st, int l) {
+    TimerScope ts(c, 2 * l);
     const int H = c->net.w[l + 1];
     dim3 grid(std::max(1, std::min<int>(c->num_sms * 8, int((c->Vcap + 127) / 128))), (H + 15) / 16);
     k_gemm_simt<ZT, MIXED><<<grid, 128, 0, c->stream>>>(c->net, st, l);
     PC_CUDA(cudaGetLastError());
+    c->launches += 1;
   }
   static void layer(pc_ctx* c, const State& st, int l, int i_begin) {
+    TimerScope ts(c, 2 * l + 1);
     const int H = c->net.w[l + 1];
     if (c->opt.exec == PC_EXEC_PERSISTENT) {
       PC_CUDA(cudaMemsetAsync(&static_cast<Global*>(c->g)->barrier, 0, sizeof(unsigned int), c->stream));
       auto fn = k_layer<ZT, MIXED>;
       NetDesc net = c->net;
       State s = st;
-      int l_ = l, ib = i_begin, mw = c->mw, rw = c->res_warps;
-      void* args[] = {&net, &s, &l_, &ib, &mw, &rw};
+      int l_ = l, ib = i_begin, mw = c->mw;
+      void* args[] = {&net, &s, &l_, &ib, &mw};
       PC_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(c->grid_persist), dim3(kBlock), args,
                                           c->res_smem, c->stream));
+      c->launches += 1;
     } else {
       for (int i = i_begin; i < H; ++i) {
-        k_sign<ZT, MIXED><<<c->grid_step, kBlock, c->res_smem, c->stream>>>(c->net, st, l, i, c->mw, c->res_warps);
+        k_sign<ZT, MIXED><<<c->grid_step, kBlock, c->res_smem, c->stream>>>(c->net, st, l, i, c->mw);
         k_edges<<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l, i);
         k_split<ZT, MIXED><<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l, i);
+        c->launches += 3;
       }
       PC_CUDA(cudaGetLastError());
     }
@@ -493,16 +567,16 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   PC_CUDA(cudaMemsetAsync(c->cnt, 0, sizeof(Counters) * (n + 1), c->stream));
 
   // launch geometry
-  const int ws = resolve_ws_doubles(mw, D);
-  c->res_warps = std::max(1, std::min(4, int((64 * 1024) / (ws * 8))));
-  c->res_smem = (size_t)c->res_warps * ws * 8;
+  c->res_smem = (size_t)newton_ws_doubles(mw, D) * 8;
   const int occ = occupancy_any(c);
   if (occ < 1) throw PcError(PC_ERR_INVALID, "persistent kernel does not fit on an SM");
   c->grid_persist = std::min(kMaxGrid, occ * c->num_sms);
   c->grid_step = std::min(kMaxGrid, 2 * c->num_sms);
 
+  for (int k = 0; k < 2 * kMaxL; ++k) c->ev_used[k] = 0;
   k_init<<<1, 256, 0, c->stream>>>(net, make_state(c));
   PC_CUDA(cudaGetLastError());
+  c->launches += 2;  // k_prep and k_init
 
   int l0 = 0, i0 = 0;
   bool gemm_done = false;
@@ -538,8 +612,28 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     gemm_done = true;
     c->grows += 1;
   }
+  const bool polish = c->opt.polish > 0 || (c->opt.polish < 0 && net.precision == PC_PREC_MIXED);
+  if (polish && net.precision != PC_PREC_FP64) {
+    double diam = 0.0;
+    for (int d = 0; d < D; ++d) diam += (hi[d] - lo[d]) * (hi[d] - lo[d]);
+    const float thr = static_cast<float>((c->opt.polish_tol > 0 ? c->opt.polish_tol : 1e-7) * std::sqrt(diam));
+    PC_CUDA(cudaFuncSetAttribute(k_polish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->res_smem));
+    k_polish<<<c->grid_step, kBlock, c->res_smem, c->stream>>>(net, make_state(c), thr, c->mw);
+    PC_CUDA(cudaGetLastError());
+    c->launches += 1;
+    PC_CUDA(cudaMemcpyAsync(c->h_g, c->g, sizeof(Global), cudaMemcpyDeviceToHost, c->stream));
+  }
   PC_CUDA(cudaMemcpyAsync(c->h_cnt, c->cnt, sizeof(Counters) * (n + 1), cudaMemcpyDeviceToHost, c->stream));
   PC_CUDA(cudaStreamSynchronize(c->stream));
+  c->polished = static_cast<Global*>(c->h_g)->polished;
+  for (int k = 0; k < 2 * kMaxL; ++k) {
+    c->ktime_ms[k] = -1.0;
+    if (c->ev_used[k]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->ev[k][0], c->ev[k][1]) == cudaSuccess) c->ktime_ms[k] = ms;
+      else cudaGetLastError();
+    }
+  }
   const Counters* hc = static_cast<const Counters*>(c->h_cnt);
   const Counters& last = hc[n];
   c->nV = last.nV_before + last.nsplit;
@@ -567,6 +661,7 @@ void StateBufs::release(pc_ctx* c) {
   ctx_free(c, Z[0]);
   ctx_free(c, Z[1]);
   ctx_free(c, esc);
+  ctx_free(c, exc);
   ctx_free(c, SIG);
   ctx_free(c, E);
   ctx_free(c, stage);
@@ -585,7 +680,9 @@ void pc_default_options(pc_options* o) {
   std::memset(o, 0, sizeof(*o));
   o->precision = PC_PREC_MIXED;
   o->exec = PC_EXEC_PERSISTENT;
-  o->filter_kappa = 2.0;
+  o->filter_kappa = 4.0;
+  o->polish = -1;
+  o->polish_tol = 1e-7;
 }
 
 pc_status pc_create(pc_ctx** out, int device, const pc_options* opt) {
@@ -622,6 +719,10 @@ pc_status pc_destroy(pc_ctx* c) {
   ctx_free(c, c->cta);
   c->release_extra();
   cudaStreamSynchronize(c->stream);
+  for (auto& e : c->ev) {
+    if (e[0]) cudaEventDestroy(e[0]);
+    if (e[1]) cudaEventDestroy(e[1]);
+  }
   if (c->h_cnt) cudaFreeHost(c->h_cnt);
   if (c->h_g) cudaFreeHost(c->h_g);
   delete c;
@@ -712,6 +813,20 @@ pc_status pc_stats(pc_ctx* c, int64_t* out, int n_neurons) {
     o[0] = s.nV_before; o[1] = s.nE_before; o[2] = s.nsplit; o[3] = s.nkeys;
     o[4] = s.npairs; o[5] = s.nfilter; o[6] = s.nundecided; o[7] = s.ndegenerate;
   }
+  return PC_OK;
+}
+
+pc_status pc_diagnostics(pc_ctx* c, int64_t* out, int n) {
+  if (!c || !out) return PC_ERR_INVALID;
+  const int64_t v[10] = {c->launches, c->grows, c->polished, c->degenerate, c->undecided,
+                         c->Vcap, c->Ecap, c->Tcap, (int64_t)c->allocated, c->grid_persist};
+  for (int k = 0; k < n && k < 10; ++k) out[k] = v[k];
+  return PC_OK;
+}
+
+pc_status pc_kernel_times(pc_ctx* c, double* out_ms, int n) {
+  if (!c || !out_ms) return PC_ERR_INVALID;
+  for (int k = 0; k < n; ++k) out_ms[k] = k < 2 * kMaxL ? c->ktime_ms[k] : -1.0;
   return PC_OK;
 }
 

@@ -25,6 +25,7 @@ struct StateBufs {
   void* X = nullptr;
   void* Z[2] = {nullptr, nullptr};
   void* esc = nullptr;
+  void* exc = nullptr;
   void* SIG = nullptr;
   void* E = nullptr;
   void* stage = nullptr;
@@ -67,14 +68,21 @@ struct pc_ctx {
   void* h_g = nullptr;
 
   // launch geometry
-  int grid_persist = 0, grid_step = 0, res_warps = 1;
+  int grid_persist = 0, grid_step = 0;
   size_t res_smem = 0;
 
   // results
   long long nV = 0, nE = 0;
   long long degenerate = 0, undecided = 0;
   long long grows = 0;
+  long long polished = 0;
+  long long launches = 0;
   bool have_result = false;
+
+  // per-layer kernel timers (opt.timers)
+  cudaEvent_t ev[2 * pc::kMaxL][2] = {};
+  int ev_used[2 * pc::kMaxL] = {};
+  double ktime_ms[2 * pc::kMaxL] = {};
 
   // adjoint scratch (allocated lazily by pc_backward)
   void* adj[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

@@ -5,8 +5,9 @@
 //   Z     [H][Vcap]   current-layer pre-activations (float32, or float64 in
 //                     FP64 mode), neuron-major so one neuron's pass reads a
 //                     contiguous row; two buffers ping-pong across layers
-//   esc   [Vcap]      float32 absolute error bound of the vertex's Z column
-//                     (mixed precision only)
+//   esc   [Vcap]      float32 estimate of the absolute error of the vertex's
+//                     FP32 Z column (FP32 and mixed precision)
+//   exc   [Vcap]      float32 estimate of the vertex's coordinate error
 //   SIG   [S][Vcap]   packed sign vectors, 2 bits per entry, word-major
 //   EU/EW [Ecap]      int32 edge endpoints (EW = EU + Ecap)
 //   stage [Ecap]      splitting-edge ids, staged per CTA range
@@ -57,7 +58,7 @@ struct NetDesc {
   double lo[kMaxD], hi[kMaxD];
   const double* W64;     // flat parameters, float64 (device copy)
   const float* W32;      // flat parameters rounded to float32
-  const float* norms;    // per layer: [2l] = max_j sum_k |W_jk|, [2l+1] = max_j |b_j|
+  const float* norms;    // per layer: [2l] = max_j ||W_j||_2, [2l+1] = max_j |b_j|
   float kappa;           // filter factor
 };
 
@@ -77,14 +78,16 @@ struct Global {
   unsigned int barrier;  // grid barrier arrival counter (reset per launch)
   unsigned int pad1;
   long long need_v, need_e, need_t;
-  long long pad[3];
+  long long polished;
+  long long pad[2];
 };
 
 struct State {
   long long Vcap, Ecap, Tcap;
   double* X;
   void* Z[2];
-  float* esc;
+  float* esc;            // FP32 value error estimate per vertex
+  float* exc;            // coordinate error estimate per vertex (absolute)
   uint64_t* SIG;
   int32_t* EU;
   int32_t* EW;

@@ -1,0 +1,205 @@
+// FP64 evaluation at the exact vertex, one CTA per vertex.
+//
+// A vertex lies on D zero entries (box facets or neuron pre-activations), all
+// affine on the vertex's own piece: the activation pattern is its stored sign
+// vector (a neuron is active iff its entry is +).  A forward pass in float64
+// with Jacobians (forward mode, D columns) from the stored coordinates gives
+// the value g and gradient of each zero entry; one Newton step on the D x D
+// system A dx = -g lands on the exact vertex (the system is affine, so one
+// step is exact up to rounding).  Used for
+//   * the filtered sign predicate: the value of neuron i at the exact vertex;
+//   * the coordinate polish: the exact vertex itself.
+#pragma once
+
+#include "pc_device.cuh"
+
+namespace pc {
+
+__host__ __device__ inline int newton_ws_doubles(int mw, int D) {
+  return 2 * mw + 2 * mw * D + D * D + 3 * D + 8;
+}
+
+struct NewtonOut {
+  double z;             // value of the target neuron at the exact vertex
+  double scale;         // sum of |terms| of that value (for the FP64 bound)
+  double dlt[kMaxD];    // Newton step
+  int ok;               // the zero set had D entries and the system was regular
+  int nz;               // number of zero entries found
+  int l_last;
+  int pad;
+};
+
+// v: vertex; e_end: entries < e_end are processed (the zero set is taken among
+// them); l_last: last layer to evaluate (-1: the highest layer of the zero
+// set); i_target: neuron of layer l_last whose exact value is wanted (-1: none).
+// All threads of the CTA must call it.  ws: newton_ws_doubles(mw, D) doubles
+// of shared memory.
+__device__ void newton_cta(const NetDesc& net, const State& st, long long v, int e_end, int l_last,
+                           int i_target, int mw, double* ws, int* s_zl, NewtonOut* out) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int D = net.D, m = net.m;
+  const long long Vcap = st.Vcap;
+  double* a = ws;
+  double* an = a + mw;
+  double* J = an + mw;
+  double* Jn = J + mw * D;
+  double* A = Jn + mw * D;
+  double* gv = A + D * D;
+  double* jt = gv + D;
+  double* misc = jt + D;
+  if (tid < 32) {
+    const int lane = tid;
+    const uint64_t zm = lane < net.S ? zero_mask(st.SIG[(long long)lane * Vcap + v], lane, e_end) : 0ull;
+    const int c = __popcll(zm);
+    int x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    int k = x - c;
+    uint64_t mm = zm;
+    while (mm) {
+      const int bit = __ffsll((long long)mm) - 1;
+      if (k < kMaxD) s_zl[k] = lane * 32 + bit / 2;
+      ++k;
+      mm &= mm - 1;
+    }
+    if (lane == 31) s_zl[kMaxD] = x;
+  }
+  if (tid < D) {
+    a[tid] = st.X[(long long)tid * Vcap + v];
+    for (int dd = 0; dd < D; ++dd) J[tid * D + dd] = (tid == dd) ? 1.0 : 0.0;
+  }
+  if (tid == 0) {
+    misc[0] = 0.0;
+    misc[1] = 0.0;
+  }
+  __syncthreads();
+  const int nz = s_zl[kMaxD];
+  const int nzc = nz < D ? nz : D;
+  if (l_last < 0) {  // highest layer among the zero-set neurons
+    l_last = -1;
+    for (int q = 0; q < nzc; ++q) {
+      const int h = s_zl[q] - m;
+      if (h < 0) continue;
+      int l = 0;
+      while (l + 1 < net.L && h >= net.off[l + 1]) ++l;
+      if (l > l_last) l_last = l;
+    }
+  }
+  int in = D;
+  for (int k = 0; k <= l_last; ++k) {
+    const int H = net.w[k + 1];
+    const double* W = net.W64 + net.wofs[k];
+    const double* b = net.W64 + net.bofs[k];
+    int tpr = 16;
+    while (tpr > 1 && H * tpr > nth) tpr >>= 1;
+    const int rows = nth / tpr;
+    for (int r0 = 0; r0 < H; r0 += rows) {
+      const int r = r0 + tid / tpr, s = tid % tpr;
+      const int entry = m + net.off[k] + r;
+      int zpos = -1;
+      for (int q = 0; q < nzc; ++q)
+        if (s_zl[q] == entry) zpos = q;
+      const bool need = r < H && (k < l_last || r == i_target || zpos >= 0);
+      double acc = 0.0, sc = 0.0, jd[kMaxD];
+#pragma unroll
+      for (int dd = 0; dd < kMaxD; ++dd) jd[dd] = 0.0;
+      if (need) {
+        const double* wr = W + (long long)r * in;
+        for (int c = s; c < in; c += tpr) {
+          const double wv = wr[c], av = a[c];
+          acc = fma(wv, av, acc);
+          sc += fabs(wv * av);
+#pragma unroll
+          for (int dd = 0; dd < kMaxD; ++dd)
+            if (dd < D) jd[dd] = fma(wv, J[c * D + dd], jd[dd]);
+        }
+      }
+      for (int o = tpr >> 1; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+#pragma unroll
+        for (int dd = 0; dd < kMaxD; ++dd) jd[dd] += __shfl_xor_sync(0xffffffffu, jd[dd], o);
+      }
+      if (need && s == 0) {
+        const double z = acc + b[r];
+        if (zpos >= 0) {
+          gv[zpos] = z;
+          for (int dd = 0; dd < D; ++dd) A[zpos * D + dd] = jd[dd];
+        }
+        if (k == l_last && r == i_target) {
+          misc[0] = z;
+          misc[1] = sc + fabs(b[r]);
+          for (int dd = 0; dd < D; ++dd) jt[dd] = jd[dd];
+        }
+        if (k < l_last) {
+          const bool act = code_at(st.SIG, Vcap, v, entry) == kPlus;
+          an[r] = act ? z : 0.0;
+          for (int dd = 0; dd < D; ++dd) Jn[r * D + dd] = act ? jd[dd] : 0.0;
+        }
+      }
+    }
+    __syncthreads();
+    double* t0 = a; a = an; an = t0;
+    double* t1 = J; J = Jn; Jn = t1;
+    in = H;
+  }
+  if (tid == 0) {
+    NewtonOut o{};
+    o.nz = nz;
+    o.l_last = l_last;
+    o.z = misc[0];
+    o.scale = misc[1];
+    if (nz == D) {
+      double M[kMaxD][kMaxD + 1];
+      for (int q = 0; q < D; ++q) {
+        const int j = s_zl[q];
+        if (j < m) {
+          const int d = j >> 1;
+          const double xd = st.X[(long long)d * Vcap + v];
+          for (int dd = 0; dd < D; ++dd) M[q][dd] = 0.0;
+          M[q][d] = (j & 1) ? -1.0 : 1.0;
+          M[q][D] = -((j & 1) ? (net.hi[d] - xd) : (xd - net.lo[d]));
+        } else {
+          for (int dd = 0; dd < D; ++dd) M[q][dd] = A[q * D + dd];
+          M[q][D] = -gv[q];
+        }
+      }
+      bool ok = true;
+      for (int c = 0; c < D && ok; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < D; ++r)
+          if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
+        if (M[piv][c] == 0.0) {
+          ok = false;
+          break;
+        }
+        if (piv != c)
+          for (int k2 = 0; k2 <= D; ++k2) {
+            const double t = M[c][k2];
+            M[c][k2] = M[piv][k2];
+            M[piv][k2] = t;
+          }
+        for (int r = c + 1; r < D; ++r) {
+          const double f = M[r][c] / M[c][c];
+          for (int k2 = c; k2 <= D; ++k2) M[r][k2] -= f * M[c][k2];
+        }
+      }
+      if (ok) {
+        for (int r = D - 1; r >= 0; --r) {
+          double acc = M[r][D];
+          for (int k2 = r + 1; k2 < D; ++k2) acc -= M[r][k2] * o.dlt[k2];
+          o.dlt[r] = acc / M[r][r];
+        }
+        if (i_target >= 0)
+          for (int dd = 0; dd < D; ++dd) o.z += jt[dd] * o.dlt[dd];
+        o.ok = 1;
+      }
+    }
+    *out = o;
+  }
+  __syncthreads();
+}
+
+}  // namespace pc

@@ -16,6 +16,7 @@
 #pragma once
 
 #include "pc_device.cuh"
+#include "pc_newton.cuh"
 
 namespace pc {
 
@@ -27,12 +28,9 @@ struct Smem {
   int zlist[kWarps][32];
   int fcount;
   int pad;
+  int nzl[kMaxD + 2];
+  NewtonOut nout;
 };
-
-// Doubles of FP64 re-evaluation workspace per warp.
-__host__ __device__ inline int resolve_ws_doubles(int mw, int D) {
-  return 2 * mw + 2 * mw * D + D * D + 3 * D + 8;
-}
 
 __device__ __forceinline__ long long warp_sum_ll(long long x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -81,153 +79,12 @@ __device__ __forceinline__ void block_scan_pref(Smem& sm, int G) {
 }
 
 // ---------------------------------------------------------------------------
-// FP64 re-evaluation of one sign (mixed precision), one warp.
-//
-// The vertex's D zero entries are affine on its own piece (activation pattern
-// = its stored sign vector, active iff +).  A forward pass with Jacobians from
-// the stored coordinates gives each zero entry's value g and gradient; one
-// Newton step on the D x D system moves to the exact vertex, and the neuron's
-// value there decides the sign.  Returns the code; writes the value to *zout.
-template <typename ZT>
-__device__ uint64_t resolve_sign(const NetDesc& net, const State& st, int l, int i, int n,
-                                 long long v, double* ws, int mw, int* zl, double* zout,
-                                 int* undecided) {
-  const int lane = threadIdx.x & 31;
-  const int D = net.D, m = net.m, e = m + n;
-  const long long Vcap = st.Vcap;
-  double* a = ws;
-  double* an = a + mw;
-  double* J = an + mw;
-  double* Jn = J + mw * D;
-  double* A = Jn + mw * D;
-  double* gv = A + D * D;
-  double* jt = gv + D;
-  double* misc = jt + D;
-  // zero entries among the processed ones (< e)
-  uint64_t zm = 0;
-  if (lane < net.S) zm = zero_mask(st.SIG[(long long)lane * Vcap + v], lane, e);
-  const int cnt = __popcll(zm);
-  int x = cnt;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  const int nz = __shfl_sync(0xffffffffu, x, 31);
-  {
-    int k = x - cnt;
-    uint64_t mm = zm;
-    while (mm) {
-      const int bit = __ffsll((long long)mm) - 1;
-      if (k < kMaxD) zl[k] = lane * 32 + bit / 2;
-      ++k;
-      mm &= mm - 1;
-    }
-  }
-  for (int d = lane; d < D; d += 32) {
-    a[d] = st.X[(long long)d * Vcap + v];
-    for (int dd = 0; dd < D; ++dd) J[d * D + dd] = (d == dd) ? 1.0 : 0.0;
-  }
-  __syncwarp();
-  const int nzc = nz < D ? nz : D;  // zero rows beyond D are never used
-  int in = D;
-  for (int k = 0; k <= l; ++k) {
-    const int H = net.w[k + 1];
-    const double* W = net.W64 + net.wofs[k];
-    const double* b = net.W64 + net.bofs[k];
-    for (int r = lane; r < H; r += 32) {
-      const int entry = m + net.off[k] + r;
-      int zpos = -1;
-      for (int q = 0; q < nzc; ++q)
-        if (zl[q] == entry) zpos = q;
-      if (k == l && r != i && zpos < 0) continue;
-      double z = b[r], sc = fabs(b[r]);
-      double jz[kMaxD];
-#pragma unroll
-      for (int dd = 0; dd < kMaxD; ++dd) jz[dd] = 0.0;
-      const double* wr = W + (long long)r * in;
-      for (int c2 = 0; c2 < in; ++c2) {
-        const double wv = wr[c2];
-        z = fma(wv, a[c2], z);
-        sc += fabs(wv * a[c2]);
-#pragma unroll
-        for (int dd = 0; dd < kMaxD; ++dd)
-          if (dd < D) jz[dd] = fma(wv, J[c2 * D + dd], jz[dd]);
-      }
-      if (zpos >= 0) {
-        gv[zpos] = z;
-        for (int dd = 0; dd < D; ++dd) A[zpos * D + dd] = jz[dd];
-      }
-      if (k == l && r == i) {
-        misc[0] = z;
-        misc[1] = sc;
-        for (int dd = 0; dd < D; ++dd) jt[dd] = jz[dd];
-      }
-      if (k < l) {
-        const bool act = code_at(st.SIG, Vcap, v, entry) == kPlus;
-        an[r] = act ? z : 0.0;
-        for (int dd = 0; dd < D; ++dd) Jn[r * D + dd] = act ? jz[dd] : 0.0;
-      }
-    }
-    __syncwarp();
-    double* t0 = a; a = an; an = t0;
-    double* t1 = J; J = Jn; Jn = t1;
-    in = H;
-  }
-  uint64_t code = kPlus;
-  if (lane == 0) {
-    double zs = misc[0];
-    if (nz == D) {
-      double M[kMaxD][kMaxD + 1];
-      for (int q = 0; q < D; ++q) {
-        const int j = zl[q];
-        if (j < m) {
-          const int d = j >> 1;
-          const double xd = st.X[(long long)d * Vcap + v];
-          for (int dd = 0; dd < D; ++dd) M[q][dd] = 0.0;
-          M[q][d] = (j & 1) ? -1.0 : 1.0;
-          M[q][D] = -((j & 1) ? (net.hi[d] - xd) : (xd - net.lo[d]));
-        } else {
-          for (int dd = 0; dd < D; ++dd) M[q][dd] = A[q * D + dd];
-          M[q][D] = -gv[q];
-        }
-      }
-      bool ok = true;
-      for (int c2 = 0; c2 < D && ok; ++c2) {
-        int piv = c2;
-        for (int r = c2 + 1; r < D; ++r)
-          if (fabs(M[r][c2]) > fabs(M[piv][c2])) piv = r;
-        if (M[piv][c2] == 0.0) { ok = false; break; }
-        if (piv != c2)
-          for (int k2 = 0; k2 <= D; ++k2) { const double t = M[c2][k2]; M[c2][k2] = M[piv][k2]; M[piv][k2] = t; }
-        for (int r = c2 + 1; r < D; ++r) {
-          const double f = M[r][c2] / M[c2][c2];
-          for (int k2 = c2; k2 <= D; ++k2) M[r][k2] -= f * M[c2][k2];
-        }
-      }
-      if (ok) {
-        double dlt[kMaxD];
-        for (int r = D - 1; r >= 0; --r) {
-          double acc = M[r][D];
-          for (int k2 = r + 1; k2 < D; ++k2) acc -= M[r][k2] * dlt[k2];
-          dlt[r] = acc / M[r][r];
-        }
-        for (int dd = 0; dd < D; ++dd) zs += jt[dd] * dlt[dd];
-      }
-    }
-    if (fabs(zs) <= 1e-12 * misc[1]) *undecided += 1;
-    code = (zs < 0.0) ? kMinus : kPlus;
-    *zout = zs;
-  }
-  code = __shfl_sync(0xffffffffu, code, 0);
-  __syncwarp();
-  return code;
-}
-
-// ---------------------------------------------------------------------------
-// Step (2).
+// Step (2).  In mixed precision a |z| within kappa times the vertex's FP32
+// error estimate is re-decided by newton_cta at the exact vertex (FP64); the
+// CTA that owns the vertex does it, all threads cooperating.
 template <typename ZT, bool MIXED>
 __device__ void phase_sign(const NetDesc& net, const State& st, int zb, int l, int i, int n,
-                           Smem& sm, double* ws_base, int mw, int res_warps) {
+                           Smem& sm, double* ws, int mw) {
   const Counters* prev = st.cnt + n;
   const long long nV = prev->nV_before + prev->nsplit;
   const long long nE = prev->nE_before + prev->nsplit + prev->npairs;
@@ -241,26 +98,25 @@ __device__ void phase_sign(const NetDesc& net, const State& st, int zb, int l, i
   const ZT* zrow = Z + (long long)i * Vcap;
   const int e = net.m + n, sh = 2 * (e & 31);
   uint64_t* sw = st.SIG + (long long)(e >> 5) * Vcap;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) sm.fcount = 0;
   __syncthreads();
   long long ndeg = 0;
   int und = 0;
   auto drain = [&]() {
     const int fc = sm.fcount;
-    if (warp < res_warps) {
-      double* ws = ws_base + (long long)warp * resolve_ws_doubles(mw, net.D);
-      for (int q = warp; q < fc; q += res_warps) {
-        const long long v = sm.flist[q];
-        double z64 = 0.0;
-        const uint64_t code = resolve_sign<ZT>(net, st, l, i, n, v, ws, mw, sm.zlist[warp], &z64, &und);
-        if (lane == 0) {
-          sw[v] = (sw[v] & ~(3ull << sh)) | (code << sh);
-          ZT zs = static_cast<ZT>(z64);
-          if (code == kPlus && !(zs > ZT(0))) zs = ZT(1e-30);
-          if (code == kMinus && !(zs < ZT(0))) zs = ZT(-1e-30);
-          Z[(long long)i * Vcap + v] = zs;
-        }
+    for (int q = 0; q < fc; ++q) {
+      const long long v = sm.flist[q];
+      newton_cta(net, st, v, e, l, i, mw, ws, sm.nzl, &sm.nout);
+      if (threadIdx.x == 0) {
+        const double zs = sm.nout.z;
+        if (fabs(zs) <= 1e-12 * sm.nout.scale || !sm.nout.ok) ++und;
+        const uint64_t code = zs < 0.0 ? kMinus : kPlus;
+        sw[v] = (sw[v] & ~(3ull << sh)) | (code << sh);
+        ZT zz = static_cast<ZT>(zs);
+        if (code == kPlus && !(zz > ZT(0))) zz = ZT(1e-30);
+        if (code == kMinus && !(zz < ZT(0))) zz = ZT(-1e-30);
+        Z[(long long)i * Vcap + v] = zz;
       }
     }
     if (threadIdx.x == 0 && fc > 0) atomic_add_ll(&cur->nfilter, (long long)fc);
@@ -289,7 +145,7 @@ __device__ void phase_sign(const NetDesc& net, const State& st, int zb, int l, i
   if (MIXED) drain();
   ndeg = warp_sum_ll(ndeg);
   if (lane == 0 && ndeg) atomic_add_ll(&cur->ndegenerate, ndeg);
-  if (MIXED && lane == 0 && und) atomic_add_ll(&cur->nundecided, (long long)und);
+  if (MIXED && threadIdx.x == 0 && und) atomic_add_ll(&cur->nundecided, (long long)und);
 }
 
 // ---------------------------------------------------------------------------
@@ -341,6 +197,7 @@ __device__ __forceinline__ void phase_edges(const NetDesc& net, const State& st,
 // Steps (4)+(5).  Returns true when capacity ran out (nothing written).
 template <typename ZT, bool MIXED>
 __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, int i, int n, Smem& sm) {
+  constexpr bool TRACK = sizeof(ZT) == 4;  // FP32 values carry error estimates
   Counters* cur = st.cnt + n + 1;
   const long long nV = cur->nV_before, nE = cur->nE_before;
   const int G = gridDim.x;
@@ -412,11 +269,20 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
     for (int j = lane; j < H; j += 32) {
       const ZT zp = Z[(long long)j * Vcap + p], zq = Z[(long long)j * Vcap + q];
       Z[(long long)j * Vcap + v0] = (j == i) ? ZT(0) : zp + tz * (zq - zp);
-      if (MIXED) amax = fmaxf(amax, fabsf(static_cast<float>(zp)) + fabsf(static_cast<float>(zq)));
+      if (TRACK) amax = fmaxf(amax, fabsf(static_cast<float>(zp)) + fabsf(static_cast<float>(zq)));
     }
-    if (MIXED) {
+    if (TRACK) {
+      // error estimates: values (rounding of the interpolation) and position
+      // (a t computed from values carrying the endpoints' estimates)
       for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-      if (lane == 0) st.esc[v0] = fmaxf(st.esc[p], st.esc[q]) + 2.4e-7f * amax;  // 4 * 2^-24
+      float dx = 0.f;
+      if (lane < D) dx = fabsf(static_cast<float>(st.X[(long long)lane * Vcap + q] - st.X[(long long)lane * Vcap + p]));
+      for (int o = 16; o > 0; o >>= 1) dx = fmaxf(dx, __shfl_xor_sync(0xffffffffu, dx, o));
+      if (lane == 0) {
+        const float ep = st.esc[p], eq = st.esc[q];
+        st.esc[v0] = fmaxf(ep, eq) + 2.4e-7f * amax;  // 4 * 2^-24
+        st.exc[v0] = fmaxf(st.exc[p], st.exc[q]) + static_cast<float>((ep + eq) / (a - b)) * dx;
+      }
     }
     // sign vector of the new vertex: join of the endpoints, entry n := 0
     uint64_t s0 = 0, zm = 0;
