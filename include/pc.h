@@ -78,16 +78,17 @@ typedef struct {
   int64_t init_ecap;      /* initial edge capacity */
   int64_t mem_budget_bytes; /* 0 = no limit */
   double filter_kappa;    /* PC_PREC_MIXED: re-evaluate a sign in FP64 when
-                             |z| <= kappa * (FP32 error estimate of z) */
-  int polish;             /* FP64 Newton polish of vertices whose coordinate
-                             error estimate exceeds polish_tol * box diameter:
-                             1 on, 0 off, -1 on in PC_PREC_MIXED only */
-  double polish_tol;      /* relative to the box diameter (default 1e-7) */
+                             |z| <= kappa * (rms FP32 error estimate of z) */
+  int polish;             /* FP64 Newton polish of every vertex whose rms
+                             coordinate error estimate exceeds polish_tol *
+                             box diameter: 1 on, 0 off, -1 on in
+                             PC_PREC_MIXED only */
+  double polish_tol;      /* relative to the box diameter (default 1e-6) */
   int timers;             /* record CUDA events around each layer's kernels */
 } pc_options;
 
 /* Fills *opt with defaults (mixed precision, persistent execution,
- * filter_kappa 4, polish in mixed precision with polish_tol 1e-7). */
+ * filter_kappa 12, polish in mixed precision with polish_tol 1e-6). */
 void pc_default_options(pc_options *opt);
 
 /* Creates a context on CUDA device `device`.  opt may be NULL (defaults). */
@@ -129,6 +130,21 @@ pc_status pc_edges(pc_ctx *ctx, const int32_t **dev, int64_t *ld, int32_t *out);
 /* Packed sign vectors, SIG[w * ld + v]; out (nullable) receives S x nV. */
 pc_status pc_signvectors(pc_ctx *ctx, const uint64_t **dev, int64_t *ld, uint64_t *out);
 
+/* The last layer's pre-activations at every vertex of the last extraction
+ * (the network output before ReLU): widths[L] x nV values, row j at
+ * out + j * nV, float32 (PC_PREC_FP32 / PC_PREC_MIXED) or float64
+ * (PC_PREC_FP64); host or device memory.  Vertices on an output neuron's
+ * zero set hold exactly 0 for it. */
+pc_status pc_values(pc_ctx *ctx, void *out);
+
+/* FP32 and mixed precision: per-vertex error estimates of the last
+ * extraction, nV floats each (host or device memory, either may be NULL).
+ * value_scale[v] = rho: the rms FP32 error of the vertex's last-layer value
+ * z_j is about ||W_j||_2 rho + 2^-25 |b_j|.  coord_rms[v]: rms estimate of the
+ * coordinate error accumulated by FP32 crossing parameters (before the
+ * polish). */
+pc_status pc_error_estimates(pc_ctx *ctx, float *value_scale, float *coord_rms);
+
 /* Per-neuron counters of the last extraction, host array of n_neurons x 8
  * int64: vertices before, edges before, splitting edges, 2-face keys, paired
  * faces, FP64 re-evaluations, undecidable signs, genericity violations. */
@@ -147,9 +163,10 @@ pc_status pc_backward(pc_ctx *ctx, const double *grad_x, double *grad_params, vo
  * capacities, device bytes held, CTAs of the persistent kernel. */
 pc_status pc_diagnostics(pc_ctx *ctx, int64_t *out, int n);
 
-/* With opt.timers: device time in ms of the last extraction's kernels per
- * layer, out_ms[2l] = layer-start forward product, out_ms[2l+1] = the neuron
- * loop of layer l (-1 where not measured). */
+/* With opt.timers: device time in ms of the last extraction's kernels,
+ * out_ms[2l] = layer-start forward product of layer l, out_ms[2l+1] = the
+ * neuron loop of layer l, out_ms[2L] = coordinate polish (-1 where not
+ * measured). */
 pc_status pc_kernel_times(pc_ctx *ctx, double *out_ms, int n);
 
 /* Message of the last error on this context ("" if none). */

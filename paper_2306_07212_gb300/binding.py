@@ -26,7 +26,7 @@ EXEC = {"persistent": 0, "stepwise": 1}
 # Every symbol include/pc.h declares (checked by the tests).
 EXPORTS = ["pc_default_options", "pc_create", "pc_destroy", "pc_set_allocator", "pc_extract",
            "pc_counts", "pc_vertices", "pc_edges", "pc_signvectors", "pc_stats", "pc_backward",
-           "pc_diagnostics", "pc_kernel_times", "pc_last_error"]
+           "pc_diagnostics", "pc_kernel_times", "pc_error_estimates", "pc_values", "pc_last_error"]
 
 
 class PcError(RuntimeError):
@@ -73,6 +73,8 @@ def load_library(path: str = LIB):
         lib.pc_stats.argtypes = [vp, i64p, ctypes.c_int]
         lib.pc_backward.argtypes = [vp, vp, vp, vp]
         lib.pc_diagnostics.argtypes = [vp, i64p, ctypes.c_int]
+        lib.pc_error_estimates.argtypes = [vp, vp, vp]
+        lib.pc_values.argtypes = [vp, vp]
         lib.pc_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         lib.pc_last_error.argtypes = [vp]
         lib.pc_last_error.restype = ctypes.c_char_p
@@ -111,7 +113,7 @@ class Extractor:
 
     def __init__(self, device: int = 0, precision: str = "mixed", execution: str = "persistent",
                  keep_tape: bool = False, strict: bool = False, init_vcap: int = 0, init_ecap: int = 0,
-                 mem_budget_bytes: int = 0, kappa: float = 4.0, polish: int = -1, polish_tol: float = 1e-7,
+                 mem_budget_bytes: int = 0, kappa: float = 12.0, polish: int = -1, polish_tol: float = 1e-6,
                  timers: bool = False, torch_allocator: bool = True):
         self._lib = load_library()
         o = Options()
@@ -232,10 +234,34 @@ class Extractor:
 
     def kernel_times_ms(self) -> np.ndarray:
         """(L, 2) ms per layer: forward product, neuron loop (-1: not measured)."""
+        return self._times()[:-1].reshape(-1, 2)
+
+    def polish_time_ms(self) -> float:
+        return float(self._times()[-1])
+
+    def _times(self) -> np.ndarray:
         L = len(self.net.widths) - 1
-        out = np.full(2 * L, -1.0)
-        self._check(self._lib.pc_kernel_times(self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 2 * L))
-        return out.reshape(L, 2)
+        out = np.full(2 * L + 1, -1.0)
+        self._check(self._lib.pc_kernel_times(self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                              2 * L + 1))
+        return out
+
+    def values(self) -> np.ndarray:
+        """(nV, H_L) last-layer pre-activations at the vertices (host copy)."""
+        c = self.counts()
+        H = self.net.widths[-1]
+        dt = np.float64 if self.options.precision == PRECISION["fp64"] else np.float32
+        out = np.empty((H, c["nV"]), dt)
+        self._check(self._lib.pc_values(self._ctx, _addr(out)))
+        return out.T
+
+    def error_estimates(self):
+        """(rho, coord_rms): per-vertex FP32 value scale and coordinate rms estimate."""
+        n = self.counts()["nV"]
+        rho = np.empty(n, np.float32)
+        crd = np.empty(n, np.float32)
+        self._check(self._lib.pc_error_estimates(self._ctx, _addr(rho), _addr(crd)))
+        return rho, crd
 
     def device_arrays(self):
         """(X ptr, ld), (E ptr, ld), (SIG ptr, ld) of the context's device buffers."""

@@ -19,8 +19,9 @@ namespace pc {
 // ---------------------------------------------------------------------------
 // Set-up kernels
 
-// float32 copy of the parameters and per-layer norms used by the FP32 error
-// estimate: max_j ||W_j||_2 and max_j |b_j| (rounded up).
+// float32 copy of the parameters, and the norms used by the FP32 error
+// estimate: per layer max_j ||W_j||_2 and max_j |b_j|, per neuron ||W_n||_2,
+// |b_n| and 1/||W_n||_2 (rounded outward).
 __global__ void k_prep(NetDesc net, float* W32, float* norms, long long n_params) {
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n_params;
        t += (long long)gridDim.x * blockDim.x)
@@ -35,8 +36,13 @@ __global__ void k_prep(NetDesc net, float* W32, float* norms, long long n_params
         const double w = net.W64[net.wofs[l] + (long long)j * K + k];
         s += w * w;
       }
+      const double bj = fabs(net.W64[net.bofs[l] + j]);
       mw = fmax(mw, sqrt(s));
-      mb = fmax(mb, fabs(net.W64[net.bofs[l] + j]));
+      mb = fmax(mb, bj);
+      float* nr = norms + 2 * kMaxL + 3 * (net.off[l] + j);
+      nr[0] = __double2float_ru(sqrt(s) * (1.0 + 1e-6));
+      nr[1] = __double2float_ru(bj);
+      nr[2] = s > 0.0 ? __double2float_rd(1.0 / (sqrt(s) * (1.0 + 1e-6))) : 0.f;
     }
     s_w[threadIdx.x] = mw;
     s_b[threadIdx.x] = mb;
@@ -82,6 +88,7 @@ __global__ void k_init(NetDesc net, State st) {
     st.cnt[0] = c0;
     Global g{};
     g.halted_at = -1;
+    g.flip_at = -1;
     *st.g = g;
   }
 }
@@ -90,6 +97,14 @@ __global__ void k_init(NetDesc net, State st) {
 // Step (1) at the start of layer l: Z_l = W_l a + b_l for every vertex, with
 // a = x (l = 0) or a_k = z_k of layer l-1 if the vertex's entry is + else 0.
 // SIMT version: one thread per vertex and 16 output neurons per block row.
+//
+// FP32 error estimate (root mean square, FP32 and mixed precision): a K-term
+// FP32 dot product accumulated in order has an rms rounding error of about
+// u/2 * S with S = sum_k |W_jk a_k| + |b_j| and u = 2^-24 (the running sums
+// are a random walk); S <= ||W_j||_2 ||a||_2 + |b_j|.  Errors already in a
+// propagate with ||W_j||_2.  Both factor as ||W_j||_2 rho(v) + u/2 |b_j|, so
+// one scale rho per vertex serves every neuron of the layer.  Layer 0 is
+// evaluated in float64 and rounded once.
 template <typename ZT, bool MIXED>
 __global__ void __launch_bounds__(128) k_gemm_simt(NetDesc net, State st, int l) {
   constexpr int TJ = 16;
@@ -123,14 +138,14 @@ __global__ void __launch_bounds__(128) k_gemm_simt(NetDesc net, State st, int l)
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nV;
        v += (long long)gridDim.x * blockDim.x) {
     ZT acc[TJ];
-    float amax = 0.f;
+    float a2 = 0.f;
     if (l == 0) {
       double dacc[TJ];
 #pragma unroll
       for (int jj = 0; jj < TJ; ++jj) dacc[jj] = bd[jj];
       for (int d = 0; d < K; ++d) {
         const double x = st.X[(long long)d * Vcap + v];
-        amax = fmaxf(amax, static_cast<float>(fabs(x)));
+        a2 += static_cast<float>(x * x);
 #pragma unroll
         for (int jj = 0; jj < TJ; ++jj) dacc[jj] = fma(Wd[jj][d], x, dacc[jj]);
       }
@@ -149,7 +164,7 @@ __global__ void __launch_bounds__(128) k_gemm_simt(NetDesc net, State st, int l)
         }
         const bool act = ((word >> (2 * (entry & 31))) & 3ull) == kPlus;
         const ZT a = act ? Zin[(long long)kk * Vcap + v] : ZT(0);
-        amax = fmaxf(amax, fabsf(static_cast<float>(a)));
+        a2 = fmaf(static_cast<float>(a), static_cast<float>(a), a2);
 #pragma unroll
         for (int jj = 0; jj < TJ; ++jj) acc[jj] = fma(Ws[jj][kk], a, acc[jj]);
       }
@@ -158,12 +173,15 @@ __global__ void __launch_bounds__(128) k_gemm_simt(NetDesc net, State st, int l)
     for (int jj = 0; jj < TJ; ++jj)
       if (j0 + jj < H) Zout[(long long)(j0 + jj) * Vcap + v] = acc[jj];
     if (TRACK && blockIdx.y == 0) {
-      // Error estimate of the FP32 column (statistical, not a worst case):
-      // rounding ~ 2u (sqrt(K) + 2)(||W_j||_2 max|a| + |b|), plus the inputs'
-      // estimate propagated through ||W_j||_2.
-      const float wn = net.norms[2 * l], bm = net.norms[2 * l + 1];
-      const float rnd = 1.2e-7f * (sqrtf(float(K)) + 2.f) * (wn * amax + bm);
-      st.esc[v] = (l == 0) ? rnd : rnd + wn * st.esc[v];
+      // rho_l: u/2 ||a||_2 (rounding: the running sums are bounded by
+      // ||W_j||_2 ||a||_2) and the largest input error of the previous layer
+      const float u = 5.9604645e-8f;  // 2^-24
+      float rho = 0.5f * u * sqrtf(a2);
+      if (l > 0) {  // independent of the rounding: add in quadrature
+        const float inh = net.norms[2 * (l - 1)] * st.esc[v] + 0.5f * u * net.norms[2 * (l - 1) + 1];
+        rho = sqrtf(rho * rho + inh * inh);
+      }
+      st.esc[v] = rho;
     }
   }
 }
@@ -176,28 +194,30 @@ __device__ __forceinline__ bool stopped(const State& st) {
 }
 
 template <typename ZT, bool MIXED>
-__global__ void __launch_bounds__(kBlock) k_sign(NetDesc net, State st, int l, int i, int mw) {
+__global__ void __launch_bounds__(kBlock, 2) k_classify(NetDesc net, State st, int l, int i, int mw) {
   extern __shared__ double dsm[];
   __shared__ Smem sm;
   if (stopped(st)) return;
-  phase_sign<ZT, MIXED>(net, st, l & 1, l, i, net.off[l] + i, sm, dsm, mw);
+  phase_classify<ZT, MIXED>(net, st, l & 1, l, i, net.off[l] + i, sm, dsm, mw);
 }
 
-__global__ void __launch_bounds__(kBlock) k_edges(NetDesc net, State st, int l, int i) {
+__global__ void __launch_bounds__(kBlock) k_reclassify(NetDesc net, State st, int l, int i) {
   __shared__ Smem sm;
   if (stopped(st)) return;
-  phase_edges(net, st, net.off[l] + i, sm);
+  const int n = net.off[l] + i;
+  if (*(volatile int*)&st.g->flip_at != n) return;
+  phase_reclassify(net, st, n, sm);
 }
 
 template <typename ZT, bool MIXED>
-__global__ void __launch_bounds__(kBlock) k_split(NetDesc net, State st, int l, int i) {
+__global__ void __launch_bounds__(kBlock, 2) k_split(NetDesc net, State st, int l, int i) {
   __shared__ Smem sm;
   if (stopped(st)) return;
   phase_split<ZT, MIXED>(net, st, l & 1, l, i, net.off[l] + i, sm);
 }
 
 template <typename ZT, bool MIXED>
-__global__ void __launch_bounds__(kBlock) k_layer(NetDesc net, State st, int l, int i_begin, int mw) {
+__global__ void __launch_bounds__(kBlock, 2) k_layer(NetDesc net, State st, int l, int i_begin, int mw) {
   extern __shared__ double dsm[];
   __shared__ Smem sm;
   if (stopped(st)) return;
@@ -205,50 +225,49 @@ __global__ void __launch_bounds__(kBlock) k_layer(NetDesc net, State st, int l, 
   const int H = net.w[l + 1];
   for (int i = i_begin; i < H; ++i) {
     const int n = net.off[l] + i;
-    phase_sign<ZT, MIXED>(net, st, l & 1, l, i, n, sm, dsm, mw);
+    phase_classify<ZT, MIXED>(net, st, l & 1, l, i, n, sm, dsm, mw);
     if (!grid_barrier(st.g, passed)) return;
-    phase_edges(net, st, n, sm);
-    if (!grid_barrier(st.g, passed)) return;
+    if (MIXED && *(volatile int*)&st.g->flip_at == n) {
+      phase_reclassify(net, st, n, sm);
+      if (!grid_barrier(st.g, passed)) return;
+    }
     if (phase_split<ZT, MIXED>(net, st, l & 1, l, i, n, sm)) return;
     if (!grid_barrier(st.g, passed)) return;
   }
 }
 
-// Coordinate polish: every vertex whose coordinate error estimate exceeds
-// thr is moved to its exact position by an FP64 Newton step on its D zero
-// entries (all entries are processed at this point).
+// Coordinate polish: every vertex whose coordinate error estimate (rms)
+// exceeds thr is moved to its exact position by an FP64 Newton step
+// on its D zero entries (all entries are processed at this point).  One warp
+// per vertex; vertices are dealt to warps round-robin.
 __global__ void __launch_bounds__(kBlock) k_polish(NetDesc net, State st, float thr, int mw) {
   extern __shared__ double dsm[];
-  __shared__ Smem sm;
+  __shared__ int zl[kWarps][kMaxD + 2];
+  __shared__ NewtonOut nout[kWarps];
   if (stopped(st)) return;
   const Counters* last = st.cnt + net.N;
   const long long nV = last->nV_before + last->nsplit;
   const long long Vcap = st.Vcap;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* ws = dsm + (long long)warp * newton_ws_doubles(mw, net.D);
   long long npol = 0;
-  if (threadIdx.x == 0) sm.fcount = 0;
-  __syncthreads();
-  for (long long base = (long long)blockIdx.x * kBlock; base < nV; base += (long long)gridDim.x * kBlock) {
-    const long long v = base + threadIdx.x;
-    if (v < nV && !(st.exc[v] <= thr)) {
-      const int slot = atomicAdd(&sm.fcount, 1);
-      sm.flist[slot] = v;
-    }
-    __syncthreads();
-    const int fc = sm.fcount;
-    for (int q = 0; q < fc; ++q) {
-      const long long u = sm.flist[q];
-      newton_cta(net, st, u, net.P, -1, -1, mw, dsm, sm.nzl, &sm.nout);
-      if (sm.nout.ok) {
-        if (threadIdx.x < net.D) st.X[(long long)threadIdx.x * Vcap + u] += sm.nout.dlt[threadIdx.x];
-        if (threadIdx.x == 0) st.exc[u] = 0.f;
-        npol += (threadIdx.x == 0);
+  const long long nwarps = (long long)gridDim.x * kWarps;
+  for (long long base = ((long long)blockIdx.x * kWarps + warp) * 32; base < nV; base += nwarps * 32) {
+    const long long v = base + lane;
+    unsigned flag = __ballot_sync(0xffffffffu, v < nV && !(st.exc[v] <= thr));
+    while (flag) {
+      const int L = __ffs(flag) - 1;
+      flag &= flag - 1;
+      const long long u = base + L;
+      newton_group<true>(net, st, u, net.P, -1, -1, mw, ws, zl[warp], &nout[warp]);
+      if (nout[warp].ok) {
+        if (lane < net.D) st.X[(long long)lane * Vcap + u] += nout[warp].dlt[lane];
+        npol += (lane == 0);
       }
+      __syncwarp();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) sm.fcount = 0;
-    __syncthreads();
   }
-  if (threadIdx.x == 0 && npol) atomic_add_ll(&st.g->polished, npol);
+  if (lane == 0 && npol) atomic_add_ll(&st.g->polished, npol);
 }
 
 }  // namespace pc
@@ -314,7 +333,7 @@ static void realloc_state(pc_ctx* c, long long V, long long E, long long T, bool
   A(nb.exc, sizeof(float) * V);
   A(nb.SIG, sizeof(uint64_t) * S * V);
   A(nb.E, sizeof(int32_t) * 2 * E);
-  A(nb.stage, sizeof(int32_t) * E);
+  A(nb.stage, sizeof(int4) * E);
   A(nb.table, sizeof(uint64_t) * T);
   if (c->opt.keep_tape) {
     A(nb.tape_pq, sizeof(int32_t) * 2 * V);
@@ -377,7 +396,7 @@ static State make_state(pc_ctx* c) {
   s.SIG = static_cast<uint64_t*>(c->bufs.SIG);
   s.EU = static_cast<int32_t*>(c->bufs.E);
   s.EW = s.EU + c->Ecap;
-  s.stage = static_cast<int32_t*>(c->bufs.stage);
+  s.stage = static_cast<int4*>(c->bufs.stage);
   s.table = static_cast<uint64_t*>(c->bufs.table);
   s.cnt = static_cast<Counters*>(c->cnt);
   s.g = static_cast<Global*>(c->g);
@@ -395,7 +414,7 @@ struct TimerScope {
   pc_ctx* c;
   int slot;
   TimerScope(pc_ctx* c_, int s) : c(c_), slot(s) {
-    if (c->opt.timers && slot < 2 * kMaxL) {
+    if (c->opt.timers && slot <= pc_ctx::kPolishSlot) {
       if (!c->ev[slot][0]) {
         cudaEventCreate(&c->ev[slot][0]);
         cudaEventCreate(&c->ev[slot][1]);
@@ -404,7 +423,7 @@ struct TimerScope {
     }
   }
   ~TimerScope() {
-    if (c->opt.timers && slot < 2 * kMaxL) {
+    if (c->opt.timers && slot <= pc_ctx::kPolishSlot) {
       cudaEventRecord(c->ev[slot][1], c->stream);
       c->ev_used[slot] = 1;
     }
@@ -436,10 +455,14 @@ struct Kernels {
       c->launches += 1;
     } else {
       for (int i = i_begin; i < H; ++i) {
-        k_sign<ZT, MIXED><<<c->grid_step, kBlock, c->res_smem, c->stream>>>(c->net, st, l, i, c->mw);
-        k_edges<<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l, i);
+        k_classify<ZT, MIXED><<<c->grid_step, kBlock, c->res_smem, c->stream>>>(c->net, st, l, i, c->mw);
+        c->launches += 1;
+        if (MIXED) {
+          k_reclassify<<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l, i);
+          c->launches += 1;
+        }
         k_split<ZT, MIXED><<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l, i);
-        c->launches += 3;
+        c->launches += 1;
       }
       PC_CUDA(cudaGetLastError());
     }
@@ -447,7 +470,7 @@ struct Kernels {
   static int occupancy(pc_ctx* c) {
     int nb = 0;
     PC_CUDA(cudaFuncSetAttribute(k_layer<ZT, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->res_smem));
-    PC_CUDA(cudaFuncSetAttribute(k_sign<ZT, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->res_smem));
+    PC_CUDA(cudaFuncSetAttribute(k_classify<ZT, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->res_smem));
     PC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_layer<ZT, MIXED>, kBlock, c->res_smem));
     return nb;
   }
@@ -528,20 +551,22 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
 
   // parameters: device copies in float64 and float32, per-layer norms
   const size_t pbytes = sizeof(double) * p;
-  if (c->params_cap < p) {
+  if (c->params_cap < p || c->norms_cap < n) {
     ctx_free(c, c->params64);
     ctx_free(c, c->params32);
     ctx_free(c, c->norms);
     c->params64 = ctx_alloc(c, pbytes);
     c->params32 = ctx_alloc(c, sizeof(float) * p);
-    c->norms = ctx_alloc(c, sizeof(float) * 2 * kMaxL);
+    c->norms = ctx_alloc(c, sizeof(float) * (2 * kMaxL + 3 * (size_t)n));
     if (!c->params64 || !c->params32 || !c->norms) throw PcError(PC_ERR_OOM, "parameter allocation failed");
     c->params_cap = p;
+    c->norms_cap = n;
   }
   PC_CUDA(cudaMemcpyAsync(c->params64, params, pbytes, cudaMemcpyDefault, c->stream));
   net.W64 = static_cast<const double*>(c->params64);
   net.W32 = static_cast<const float*>(c->params32);
   net.norms = static_cast<const float*>(c->norms);
+  net.nrm = net.norms + 2 * kMaxL;
   k_prep<<<std::max(L, 64), 256, 0, c->stream>>>(net, static_cast<float*>(c->params32), static_cast<float*>(c->norms), p);
   PC_CUDA(cudaGetLastError());
 
@@ -573,7 +598,7 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   c->grid_persist = std::min(kMaxGrid, occ * c->num_sms);
   c->grid_step = std::min(kMaxGrid, 2 * c->num_sms);
 
-  for (int k = 0; k < 2 * kMaxL; ++k) c->ev_used[k] = 0;
+  for (int k = 0; k <= pc_ctx::kPolishSlot; ++k) c->ev_used[k] = 0;
   k_init<<<1, 256, 0, c->stream>>>(net, make_state(c));
   PC_CUDA(cudaGetLastError());
   c->launches += 2;  // k_prep and k_init
@@ -616,9 +641,11 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   if (polish && net.precision != PC_PREC_FP64) {
     double diam = 0.0;
     for (int d = 0; d < D; ++d) diam += (hi[d] - lo[d]) * (hi[d] - lo[d]);
-    const float thr = static_cast<float>((c->opt.polish_tol > 0 ? c->opt.polish_tol : 1e-7) * std::sqrt(diam));
-    PC_CUDA(cudaFuncSetAttribute(k_polish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->res_smem));
-    k_polish<<<c->grid_step, kBlock, c->res_smem, c->stream>>>(net, make_state(c), thr, c->mw);
+    const float thr = static_cast<float>((c->opt.polish_tol > 0 ? c->opt.polish_tol : 1e-6) * std::sqrt(diam));
+    const size_t psmem = c->res_smem * kWarps;
+    PC_CUDA(cudaFuncSetAttribute(k_polish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
+    TimerScope ts(c, pc_ctx::kPolishSlot);
+    k_polish<<<c->grid_step, kBlock, psmem, c->stream>>>(net, make_state(c), thr, c->mw);
     PC_CUDA(cudaGetLastError());
     c->launches += 1;
     PC_CUDA(cudaMemcpyAsync(c->h_g, c->g, sizeof(Global), cudaMemcpyDeviceToHost, c->stream));
@@ -626,7 +653,7 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   PC_CUDA(cudaMemcpyAsync(c->h_cnt, c->cnt, sizeof(Counters) * (n + 1), cudaMemcpyDeviceToHost, c->stream));
   PC_CUDA(cudaStreamSynchronize(c->stream));
   c->polished = static_cast<Global*>(c->h_g)->polished;
-  for (int k = 0; k < 2 * kMaxL; ++k) {
+  for (int k = 0; k <= pc_ctx::kPolishSlot; ++k) {
     c->ktime_ms[k] = -1.0;
     if (c->ev_used[k]) {
       float ms = 0.f;
@@ -680,9 +707,9 @@ void pc_default_options(pc_options* o) {
   std::memset(o, 0, sizeof(*o));
   o->precision = PC_PREC_MIXED;
   o->exec = PC_EXEC_PERSISTENT;
-  o->filter_kappa = 4.0;
+  o->filter_kappa = 12.0;
   o->polish = -1;
-  o->polish_tol = 1e-7;
+  o->polish_tol = 1e-6;
 }
 
 pc_status pc_create(pc_ctx** out, int device, const pc_options* opt) {
@@ -802,6 +829,22 @@ pc_status pc_signvectors(pc_ctx* c, const uint64_t** dev, int64_t* ld, uint64_t*
   return copy_rows(c, out, c->bufs.SIG, 8, c->Vcap, c->nV, c->net.S);
 }
 
+pc_status pc_values(pc_ctx* c, void* out) {
+  if (!c) return PC_ERR_INVALID;
+  if (!c->have_result) return c->fail(PC_ERR_INVALID, "no extraction result");
+  const int L = c->net.L;
+  return copy_rows(c, out, c->bufs.Z[(L - 1) & 1], zsize_of(c->net.precision), c->Vcap, c->nV, c->net.w[L]);
+}
+
+pc_status pc_error_estimates(pc_ctx* c, float* value_scale, float* coord_rms) {
+  if (!c) return PC_ERR_INVALID;
+  if (!c->have_result) return c->fail(PC_ERR_INVALID, "no extraction result");
+  if (c->net.precision == PC_PREC_FP64) return c->fail(PC_ERR_INVALID, "no FP32 error estimates in FP64 mode");
+  pc_status s = copy_rows(c, value_scale, c->bufs.esc, 4, c->Vcap, c->nV, 1);
+  if (s != PC_OK) return s;
+  return copy_rows(c, coord_rms, c->bufs.exc, 4, c->Vcap, c->nV, 1);
+}
+
 pc_status pc_stats(pc_ctx* c, int64_t* out, int n_neurons) {
   if (!c || !out) return PC_ERR_INVALID;
   if (!c->have_result) return c->fail(PC_ERR_INVALID, "no extraction result");
@@ -826,7 +869,8 @@ pc_status pc_diagnostics(pc_ctx* c, int64_t* out, int n) {
 
 pc_status pc_kernel_times(pc_ctx* c, double* out_ms, int n) {
   if (!c || !out_ms) return PC_ERR_INVALID;
-  for (int k = 0; k < n; ++k) out_ms[k] = k < 2 * kMaxL ? c->ktime_ms[k] : -1.0;
+  const int L2 = 2 * c->net.L;
+  for (int k = 0; k < n; ++k) out_ms[k] = k < L2 ? c->ktime_ms[k] : (k == L2 ? c->ktime_ms[pc_ctx::kPolishSlot] : -1.0);
   return PC_OK;
 }
 

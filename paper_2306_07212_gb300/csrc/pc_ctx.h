@@ -54,6 +54,7 @@ struct pc_ctx {
   void* params32 = nullptr;
   void* norms = nullptr;
   long long params_cap = 0;
+  int norms_cap = 0;
 
   // state
   StateBufs bufs;
@@ -80,9 +81,10 @@ struct pc_ctx {
   bool have_result = false;
 
   // per-layer kernel timers (opt.timers)
-  cudaEvent_t ev[2 * pc::kMaxL][2] = {};
-  int ev_used[2 * pc::kMaxL] = {};
-  double ktime_ms[2 * pc::kMaxL] = {};
+  static constexpr int kPolishSlot = 2 * pc::kMaxL;
+  cudaEvent_t ev[2 * pc::kMaxL + 1][2] = {};
+  int ev_used[2 * pc::kMaxL + 1] = {};
+  double ktime_ms[2 * pc::kMaxL + 1] = {};
 
   // adjoint scratch (allocated lazily by pc_backward)
   void* adj[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

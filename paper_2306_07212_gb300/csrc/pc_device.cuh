@@ -5,12 +5,13 @@
 //   Z     [H][Vcap]   current-layer pre-activations (float32, or float64 in
 //                     FP64 mode), neuron-major so one neuron's pass reads a
 //                     contiguous row; two buffers ping-pong across layers
-//   esc   [Vcap]      float32 estimate of the absolute error of the vertex's
-//                     FP32 Z column (FP32 and mixed precision)
+//   esc   [Vcap]      float32 error scale rho of the vertex's FP32 Z column:
+//                     the rms error of z_j is about ||W_j||_2 rho + u/2 |b_j|
+//                     (FP32 and mixed precision)
 //   exc   [Vcap]      float32 estimate of the vertex's coordinate error
 //   SIG   [S][Vcap]   packed sign vectors, 2 bits per entry, word-major
 //   EU/EW [Ecap]      int32 edge endpoints (EW = EU + Ecap)
-//   stage [Ecap]      splitting-edge ids, staged per CTA range
+//   stage [Ecap]      splitting edges (edge id, V+, V-), staged per CTA range
 //   table [Tcap]      open-addressing hash table of 2-face keys
 //   cnt   [N+1]       per-neuron counters (slot n+1 belongs to neuron n)
 #pragma once
@@ -35,7 +36,7 @@ constexpr uint64_t kPaired = 1ull << 31; // payload flag: face already paired
 
 constexpr int kBlock = 512;              // threads per CTA in the neuron phases
 constexpr int kWarps = kBlock / 32;
-constexpr int kMaxGrid = 2048;           // upper bound on CTAs of a phase grid
+constexpr int kMaxGrid = 1024;           // upper bound on CTAs of a phase grid
 constexpr int kFilterCap = 2 * kBlock;   // CTA-local list of filtered vertices
 
 // error bits in Global::error
@@ -59,6 +60,7 @@ struct NetDesc {
   const double* W64;     // flat parameters, float64 (device copy)
   const float* W32;      // flat parameters rounded to float32
   const float* norms;    // per layer: [2l] = max_j ||W_j||_2, [2l+1] = max_j |b_j|
+  const float* nrm;      // per neuron n: [3n] = ||W_n||_2, [3n+1] = |b_n|, [3n+2] = 1/||W_n||_2
   float kappa;           // filter factor
 };
 
@@ -74,7 +76,7 @@ struct Global {
   int halted_at;         // -1, or the neuron whose step ran out of capacity
   int halt_reason;
   int error;             // sticky kErr* bits
-  int pad0;
+  int flip_at;           // last neuron whose FP64 re-decision flipped a sign
   unsigned int barrier;  // grid barrier arrival counter (reset per launch)
   unsigned int pad1;
   long long need_v, need_e, need_t;
@@ -91,7 +93,7 @@ struct State {
   uint64_t* SIG;
   int32_t* EU;
   int32_t* EW;
-  int32_t* stage;
+  int4* stage;           // splitting edges (edge, V+, V-, 0) staged per CTA range
   uint64_t* table;
   Counters* cnt;
   Global* g;

@@ -1,12 +1,13 @@
-// FP64 evaluation at the exact vertex, one CTA per vertex.
+// FP64 evaluation at the exact vertex, one CTA or one warp per vertex.
 //
 // A vertex lies on D zero entries (box facets or neuron pre-activations), all
 // affine on the vertex's own piece: the activation pattern is its stored sign
-// vector (a neuron is active iff its entry is +).  A forward pass in float64
-// with Jacobians (forward mode, D columns) from the stored coordinates gives
-// the value g and gradient of each zero entry; one Newton step on the D x D
-// system A dx = -g lands on the exact vertex (the system is affine, so one
-// step is exact up to rounding).  Used for
+// vector (a neuron is active iff its entry is +).  A forward pass from the
+// stored coordinates gives the value g (float64) and gradient (float32,
+// forward mode, D columns) of each zero entry; one Newton step on the D x D
+// system A dx = -g lands on the exact vertex: the system is affine, and the
+// step is small (the stored coordinates are FP32-accurate), so the float32
+// gradient adds only (1e-7 relative) x (step) to the result.  Used for
 //   * the filtered sign predicate: the value of neuron i at the exact vertex;
 //   * the coordinate polish: the exact vertex itself.
 #pragma once
@@ -16,7 +17,7 @@
 namespace pc {
 
 __host__ __device__ inline int newton_ws_doubles(int mw, int D) {
-  return 2 * mw + 2 * mw * D + D * D + 3 * D + 8;
+  return 2 * mw + mw * D + D * D + 3 * D + 8 + kMaxWords;  // J, Jn are float
 }
 
 struct NewtonOut {
@@ -32,24 +33,30 @@ struct NewtonOut {
 // v: vertex; e_end: entries < e_end are processed (the zero set is taken among
 // them); l_last: last layer to evaluate (-1: the highest layer of the zero
 // set); i_target: neuron of layer l_last whose exact value is wanted (-1: none).
-// All threads of the CTA must call it.  ws: newton_ws_doubles(mw, D) doubles
-// of shared memory.
-__device__ void newton_cta(const NetDesc& net, const State& st, long long v, int e_end, int l_last,
-                           int i_target, int mw, double* ws, int* s_zl, NewtonOut* out) {
-  const int tid = threadIdx.x, nth = blockDim.x;
+// WARP = false: all threads of the CTA call it; WARP = true: all lanes of one
+// warp call it (ws, s_zl and out private to the warp).  ws holds
+// newton_ws_doubles(mw, D) doubles of shared memory.
+template <bool WARP>
+__device__ void newton_group(const NetDesc& net, const State& st, long long v, int e_end, int l_last,
+                             int i_target, int mw, double* ws, int* s_zl, NewtonOut* out) {
+  const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
+  const int nth = WARP ? 32 : blockDim.x;
   const int D = net.D, m = net.m;
   const long long Vcap = st.Vcap;
   double* a = ws;
   double* an = a + mw;
-  double* J = an + mw;
-  double* Jn = J + mw * D;
-  double* A = Jn + mw * D;
+  float* J = reinterpret_cast<float*>(an + mw);
+  float* Jn = J + mw * D;
+  double* A = reinterpret_cast<double*>(Jn + mw * D);
   double* gv = A + D * D;
   double* jt = gv + D;
   double* misc = jt + D;
+  uint64_t* sig = reinterpret_cast<uint64_t*>(misc + 8);  // the vertex's sign words
   if (tid < 32) {
     const int lane = tid;
-    const uint64_t zm = lane < net.S ? zero_mask(st.SIG[(long long)lane * Vcap + v], lane, e_end) : 0ull;
+    const uint64_t word = lane < net.S ? st.SIG[(long long)lane * Vcap + v] : 0ull;
+    if (lane < net.S) sig[lane] = word;
+    const uint64_t zm = lane < net.S ? zero_mask(word, lane, e_end) : 0ull;
     const int c = __popcll(zm);
     int x = c;
     for (int o = 1; o < 32; o <<= 1) {
@@ -68,13 +75,13 @@ __device__ void newton_cta(const NetDesc& net, const State& st, long long v, int
   }
   if (tid < D) {
     a[tid] = st.X[(long long)tid * Vcap + v];
-    for (int dd = 0; dd < D; ++dd) J[tid * D + dd] = (tid == dd) ? 1.0 : 0.0;
+    for (int dd = 0; dd < D; ++dd) J[tid * D + dd] = (tid == dd) ? 1.f : 0.f;
   }
   if (tid == 0) {
     misc[0] = 0.0;
     misc[1] = 0.0;
   }
-  __syncthreads();
+  if (WARP) __syncwarp(); else __syncthreads();
   const int nz = s_zl[kMaxD];
   const int nzc = nz < D ? nz : D;
   if (l_last < 0) {  // highest layer among the zero-set neurons
@@ -91,6 +98,7 @@ __device__ void newton_cta(const NetDesc& net, const State& st, long long v, int
   for (int k = 0; k <= l_last; ++k) {
     const int H = net.w[k + 1];
     const double* W = net.W64 + net.wofs[k];
+    const float* W32 = net.W32 + net.wofs[k];
     const double* b = net.W64 + net.bofs[k];
     int tpr = 16;
     while (tpr > 1 && H * tpr > nth) tpr >>= 1;
@@ -102,18 +110,21 @@ __device__ void newton_cta(const NetDesc& net, const State& st, long long v, int
       for (int q = 0; q < nzc; ++q)
         if (s_zl[q] == entry) zpos = q;
       const bool need = r < H && (k < l_last || r == i_target || zpos >= 0);
-      double acc = 0.0, sc = 0.0, jd[kMaxD];
+      double acc = 0.0;
+      float sc = 0.f, jd[kMaxD];
 #pragma unroll
-      for (int dd = 0; dd < kMaxD; ++dd) jd[dd] = 0.0;
+      for (int dd = 0; dd < kMaxD; ++dd) jd[dd] = 0.f;
       if (need) {
         const double* wr = W + (long long)r * in;
+        const float* wr32 = W32 + (long long)r * in;
         for (int c = s; c < in; c += tpr) {
-          const double wv = wr[c], av = a[c];
-          acc = fma(wv, av, acc);
-          sc += fabs(wv * av);
+          const double av = a[c];
+          acc = fma(wr[c], av, acc);
+          const float w32 = wr32[c];
+          sc = fmaf(fabsf(w32), fabsf(static_cast<float>(av)), sc);
 #pragma unroll
           for (int dd = 0; dd < kMaxD; ++dd)
-            if (dd < D) jd[dd] = fma(wv, J[c * D + dd], jd[dd]);
+            if (dd < D) jd[dd] = fmaf(w32, J[c * D + dd], jd[dd]);
         }
       }
       for (int o = tpr >> 1; o > 0; o >>= 1) {
@@ -134,15 +145,15 @@ __device__ void newton_cta(const NetDesc& net, const State& st, long long v, int
           for (int dd = 0; dd < D; ++dd) jt[dd] = jd[dd];
         }
         if (k < l_last) {
-          const bool act = code_at(st.SIG, Vcap, v, entry) == kPlus;
+          const bool act = ((sig[entry >> 5] >> (2 * (entry & 31))) & 3ull) == kPlus;
           an[r] = act ? z : 0.0;
-          for (int dd = 0; dd < D; ++dd) Jn[r * D + dd] = act ? jd[dd] : 0.0;
+          for (int dd = 0; dd < D; ++dd) Jn[r * D + dd] = act ? jd[dd] : 0.f;
         }
       }
     }
-    __syncthreads();
+    if (WARP) __syncwarp(); else __syncthreads();
     double* t0 = a; a = an; an = t0;
-    double* t1 = J; J = Jn; Jn = t1;
+    float* t1 = J; J = Jn; Jn = t1;
     in = H;
   }
   if (tid == 0) {
@@ -199,7 +210,13 @@ __device__ void newton_cta(const NetDesc& net, const State& st, long long v, int
     }
     *out = o;
   }
-  __syncthreads();
+  if (WARP) __syncwarp(); else __syncthreads();
+}
+
+__device__ __forceinline__ void newton_cta(const NetDesc& net, const State& st, long long v, int e_end,
+                                           int l_last, int i_target, int mw, double* ws, int* s_zl,
+                                           NewtonOut* out) {
+  newton_group<false>(net, st, v, e_end, l_last, i_target, mw, ws, s_zl, out);
 }
 
 }  // namespace pc

@@ -1,18 +1,25 @@
 // The per-neuron steps of edge subdivision (Section 4.2) as device functions.
 //
-// One neuron step is three phases separated by grid-wide synchronisation
-// (a kernel boundary in stepwise execution, a grid barrier in the persistent
+// One neuron step is two phases separated by grid-wide synchronisation (a
+// kernel boundary in stepwise execution, a grid barrier in the persistent
 // per-layer kernel):
-//   phase_sign   step (2): the sign of every vertex w.r.t. the neuron's folded
-//                hyperplane, from the stored pre-activation; in mixed precision
-//                any |z| within its error bound is re-decided in FP64.
-//   phase_edges  step (3): warp-ballot compaction of the splitting edges
-//                (endpoint signs differ), order-preserving per CTA range.
-//   phase_split  steps (4)+(5): one warp per splitting edge interpolates the
-//                new vertex (FP64 t and coordinates, values in the Z type),
-//                splits the edge, and inserts the edge's parent 2-face keys
-//                into a hash table; the second arrival of a face emits the
-//                intersecting edge.
+//
+//   phase_classify  steps (2)+(3).  Every vertex's sign w.r.t. the neuron's
+//       folded hyperplane is written into its sign vector; in the same pass
+//       every edge is classified from the signs of its endpoints' stored
+//       values (splitting iff they differ) and the splitting edges are
+//       compacted per CTA range with warp ballots and a block scan, keeping
+//       edge order.  In mixed precision a |z| within kappa times its FP32
+//       error estimate is re-decided in FP64 at the exact vertex; the edge
+//       pass used the FP32 sign, so if a re-decision flips a sign the step is
+//       marked and the edges are classified again from the final signs
+//       (phase_reclassify) before splitting.
+//
+//   phase_split  steps (4)+(5).  One warp per splitting edge interpolates the
+//       new vertex (FP64 t and coordinates, values in the value type), splits
+//       the edge into E+ and E-, and inserts the edge's parent 2-face keys
+//       into an open-addressing hash table.  The second arrival of a 2-face
+//       verifies the match exactly and emits the intersecting edge.
 #pragma once
 
 #include "pc_device.cuh"
@@ -20,16 +27,20 @@
 
 namespace pc {
 
+constexpr int kPairCap = 2048;   // intersecting edges a CTA buffers per step
+
 struct Smem {
   long long pref[kMaxGrid + 1];
   long long wsum[kWarps + 1];
   long long flist[kFilterCap];
-  uint64_t s0row[kWarps][kMaxWords];
   int zlist[kWarps][32];
+  int2 pairs[kPairCap];
+  int npairs;
   int fcount;
-  int pad;
+  int flip;
   int nzl[kMaxD + 2];
   NewtonOut nout;
+  long long acc[4];
 };
 
 __device__ __forceinline__ long long warp_sum_ll(long long x) {
@@ -78,13 +89,111 @@ __device__ __forceinline__ void block_scan_pref(Smem& sm, int G) {
   __syncthreads();
 }
 
+// Block-wide exclusive scan of one small count per thread; returns the
+// thread's offset and leaves the block total in sm.wsum[kWarps].
+__device__ __forceinline__ int block_offsets(Smem& sm, int c) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sm.wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const long long w = lane < kWarps ? sm.wsum[lane] : 0;
+    long long xx = w;
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, xx, o);
+      if (lane >= o) xx += y;
+    }
+    if (lane < kWarps) sm.wsum[lane] = xx - w;
+    if (lane == kWarps - 1) sm.wsum[kWarps] = xx;
+  }
+  __syncthreads();
+  return int(sm.wsum[warp]) + x - c;
+}
+
+// Edge range of this CTA in the compaction (a multiple of 4 edges per CTA).
+__device__ __forceinline__ void cta_range(long long nE, long long& chunk, long long& begin, long long& end) {
+  const long long G = gridDim.x;
+  chunk = ((nE + G - 1) / G + 3) & ~3ll;
+  begin = blockIdx.x * chunk;
+  if (begin > nE) begin = nE;
+  end = begin + chunk < nE ? begin + chunk : nE;
+}
+
+// Compacts the splitting edges of [begin, end) into stage[begin ...] in edge
+// order as (edge, V+, V-).  FROM_CODES: classify from the stored sign codes
+// (after every sign is final); otherwise from the sign of the stored value.
+template <typename ZT, bool FROM_CODES>
+__device__ long long compact_edges(const State& st, const ZT* zrow, int e, long long begin, long long end,
+                                   Smem& sm) {
+  const int sh = 2 * (e & 31);
+  const uint64_t* sw = st.SIG + (long long)(e >> 5) * st.Vcap;
+  long long count = 0;
+  for (long long base = begin; base < end; base += 4 * kBlock) {
+    const long long idx0 = base + 4 * threadIdx.x;
+    int4 eu = make_int4(0, 0, 0, 0), ew = make_int4(0, 0, 0, 0);
+    int nvalid = 0;
+    if (idx0 < end) {
+      nvalid = end - idx0 >= 4 ? 4 : int(end - idx0);
+      if (nvalid == 4) {
+        eu = *reinterpret_cast<const int4*>(st.EU + idx0);
+        ew = *reinterpret_cast<const int4*>(st.EW + idx0);
+      } else {
+        int* pu = &eu.x;
+        int* pw = &ew.x;
+        for (int q = 0; q < nvalid; ++q) {
+          pu[q] = st.EU[idx0 + q];
+          pw[q] = st.EW[idx0 + q];
+        }
+      }
+    }
+    const int* pu = &eu.x;
+    const int* pw = &ew.x;
+    bool uplus[4], split[4];
+    int c = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      split[q] = false;
+      uplus[q] = true;
+      if (q < nvalid) {
+        bool su, sv;
+        if (FROM_CODES) {
+          su = ((sw[pu[q]] >> sh) & 3ull) == kMinus;
+          sv = ((sw[pw[q]] >> sh) & 3ull) == kMinus;
+        } else {
+          su = zrow[pu[q]] < ZT(0);
+          sv = zrow[pw[q]] < ZT(0);
+        }
+        split[q] = su != sv;
+        uplus[q] = !su;
+        c += split[q];
+      }
+    }
+    const int off = block_offsets(sm, c);
+    int k = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (split[q]) {
+        const int p = uplus[q] ? pu[q] : pw[q];
+        const int mq = uplus[q] ? pw[q] : pu[q];
+        st.stage[begin + count + off + k] = make_int4(int(idx0 + q), p, mq, 0);
+        ++k;
+      }
+    }
+    count += sm.wsum[kWarps];
+    __syncthreads();
+  }
+  return count;
+}
+
 // ---------------------------------------------------------------------------
-// Step (2).  In mixed precision a |z| within kappa times the vertex's FP32
-// error estimate is re-decided by newton_cta at the exact vertex (FP64); the
-// CTA that owns the vertex does it, all threads cooperating.
+// Steps (2)+(3).
 template <typename ZT, bool MIXED>
-__device__ void phase_sign(const NetDesc& net, const State& st, int zb, int l, int i, int n,
-                           Smem& sm, double* ws, int mw) {
+__device__ void phase_classify(const NetDesc& net, const State& st, int zb, int l, int i, int n,
+                               Smem& sm, double* ws, int mw) {
   const Counters* prev = st.cnt + n;
   const long long nV = prev->nV_before + prev->nsplit;
   const long long nE = prev->nE_before + prev->nsplit + prev->npairs;
@@ -99,10 +208,15 @@ __device__ void phase_sign(const NetDesc& net, const State& st, int zb, int l, i
   const int e = net.m + n, sh = 2 * (e & 31);
   uint64_t* sw = st.SIG + (long long)(e >> 5) * Vcap;
   const int lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) sm.fcount = 0;
+  if (threadIdx.x == 0) {
+    sm.fcount = 0;
+    sm.flip = 0;
+  }
   __syncthreads();
   long long ndeg = 0;
   int und = 0;
+  // FP64 re-decision of the CTA's filtered vertices, one at a time with all
+  // threads cooperating (newton_cta).
   auto drain = [&]() {
     const int fc = sm.fcount;
     for (int q = 0; q < fc; ++q) {
@@ -112,6 +226,8 @@ __device__ void phase_sign(const NetDesc& net, const State& st, int zb, int l, i
         const double zs = sm.nout.z;
         if (fabs(zs) <= 1e-12 * sm.nout.scale || !sm.nout.ok) ++und;
         const uint64_t code = zs < 0.0 ? kMinus : kPlus;
+        const bool spec_minus = zrow[v] < ZT(0);
+        if (spec_minus != (code == kMinus)) sm.flip = 1;
         sw[v] = (sw[v] & ~(3ull << sh)) | (code << sh);
         ZT zz = static_cast<ZT>(zs);
         if (code == kPlus && !(zz > ZT(0))) zz = ZT(1e-30);
@@ -124,12 +240,17 @@ __device__ void phase_sign(const NetDesc& net, const State& st, int zb, int l, i
     if (threadIdx.x == 0) sm.fcount = 0;
     __syncthreads();
   };
-  for (long long base = (long long)blockIdx.x * kBlock; base < nV; base += (long long)gridDim.x * kBlock) {
-    const long long v = base + threadIdx.x;
+  const float nr_i = net.nrm[3 * n], b_i = 2.9802322e-8f * net.nrm[3 * n + 1];
+  // step (2): the signs; 32-vertex tiles are dealt round-robin over the CTAs
+  // so that neighbouring vertices (often filtered together) spread out
+  const long long G = gridDim.x;
+  const int warp = threadIdx.x >> 5;
+  for (long long round = 0; round * G * kBlock < nV; ++round) {
+    const long long v = ((round * kWarps + warp) * G + blockIdx.x) * 32 + lane;
     if (v < nV) {
       const ZT z = zrow[v];
       bool filt = false;
-      if (MIXED) filt = fabsf(static_cast<float>(z)) <= net.kappa * st.esc[v];
+      if (MIXED) filt = fabsf(static_cast<float>(z)) <= net.kappa * (nr_i * st.esc[v] + b_i);
       if (filt) {
         const int slot = atomicAdd(&sm.fcount, 1);
         sm.flist[slot] = v;
@@ -139,58 +260,85 @@ __device__ void phase_sign(const NetDesc& net, const State& st, int zb, int l, i
         sw[v] = (sw[v] & ~(3ull << sh)) | (code << sh);
       }
     }
-    __syncthreads();
-    if (sm.fcount > kFilterCap - kBlock) drain();
+    if (MIXED) {
+      __syncthreads();
+      if (sm.fcount > kFilterCap - kBlock) drain();
+    }
   }
-  if (MIXED) drain();
+  if (MIXED) {
+    __syncthreads();
+    drain();
+    if (threadIdx.x == 0 && sm.flip) atomicMax(&st.g->flip_at, n);
+  }
+  // the part of the hash table that the previous neuron used
+  const long long tprev = st.cnt[n].tsize;
+  for (long long t = (long long)blockIdx.x * kBlock + threadIdx.x; t < tprev; t += (long long)gridDim.x * kBlock)
+    st.table[t] = kEmpty;
+  // step (3): splitting edges, speculatively from the signs of the values
+  long long chunk, begin, end;
+  cta_range(nE, chunk, begin, end);
+  const long long count = compact_edges<ZT, false>(st, zrow, e, begin, end, sm);
+  if (threadIdx.x == 0) st.cta_count[blockIdx.x] = count;
   ndeg = warp_sum_ll(ndeg);
   if (lane == 0 && ndeg) atomic_add_ll(&cur->ndegenerate, ndeg);
   if (MIXED && threadIdx.x == 0 && und) atomic_add_ll(&cur->nundecided, (long long)und);
 }
 
-// ---------------------------------------------------------------------------
-// Step (3).
-__device__ __forceinline__ void phase_edges(const NetDesc& net, const State& st, int n, Smem& sm) {
-  const Counters* cur = st.cnt + n + 1;
-  const long long nE = cur->nE_before;
-  // clear the part of the hash table that the previous neuron used
-  const long long tprev = st.cnt[n].tsize;
-  for (long long t = (long long)blockIdx.x * kBlock + threadIdx.x; t < tprev; t += (long long)gridDim.x * kBlock)
-    st.table[t] = kEmpty;
-  const long long G = gridDim.x;
-  const long long chunk = (nE + G - 1) / G;
-  const long long begin = blockIdx.x * chunk;
-  const long long end = begin + chunk < nE ? begin + chunk : nE;
-  const int e = net.m + n, sh = 2 * (e & 31);
-  const uint64_t* sw = st.SIG + (long long)(e >> 5) * st.Vcap;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  long long count = 0;
-  for (long long base = begin; base < end; base += kBlock) {
-    const long long idx = base + threadIdx.x;
-    bool split = false;
-    if (idx < end) {
-      const int32_t u = st.EU[idx], w = st.EW[idx];
-      split = ((sw[u] >> sh) & 3ull) != ((sw[w] >> sh) & 3ull);
-    }
-    const unsigned mask = __ballot_sync(0xffffffffu, split);
-    if (lane == 0) sm.wsum[warp] = __popc(mask);
-    __syncthreads();
-    if (warp == 0) {
-      const long long c = lane < kWarps ? sm.wsum[lane] : 0;
-      long long x = c;
-      for (int o = 1; o < 32; o <<= 1) {
-        const long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      if (lane < kWarps) sm.wsum[lane] = x - c;
-      if (lane == kWarps - 1) sm.wsum[kWarps] = x;
-    }
-    __syncthreads();
-    if (split) st.stage[begin + count + sm.wsum[warp] + __popc(mask & ((1u << lane) - 1u))] = int32_t(idx);
-    count += sm.wsum[kWarps];
-    __syncthreads();
-  }
+// Step (3) again from the final sign codes, for a step whose FP64 re-decision
+// flipped a sign that the speculative pass had used.
+__device__ __forceinline__ void phase_reclassify(const NetDesc& net, const State& st, int n, Smem& sm) {
+  const long long nE = st.cnt[n + 1].nE_before;
+  long long chunk, begin, end;
+  cta_range(nE, chunk, begin, end);
+  const long long count = compact_edges<float, true>(st, nullptr, net.m + n, begin, end, sm);
   if (threadIdx.x == 0) st.cta_count[blockIdx.x] = count;
+}
+
+// Whole-warp check that the 2-face key of split edge k2 (payload r2 =
+// 2 * zero ordinal + minus) equals F, where lane w holds word w of the
+// splitting edge's sign vector s0 and F is s0 with word wj replaced by Fw.
+// The partner's key is rebuilt from its staged endpoints, which this phase
+// does not modify, so no memory fence is needed.  All lanes must call it.
+__device__ __forceinline__ bool warp_face_matches(const State& st, const Smem& sm, int G, long long chunk,
+                                                  long long k2, int r2, int e, int S, uint64_t s0,
+                                                  int wj, uint64_t Fw) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = G - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sm.pref[mid] <= k2) lo = mid; else hi = mid - 1;
+  }
+  const int4 s2 = st.stage[lo * chunk + (k2 - sm.pref[lo])];
+  const long long Vcap = st.Vcap;
+  const int wn = e >> 5, sh = 2 * (e & 31);
+  uint64_t w2 = 0, zm = 0;
+  if (lane < S) {
+    w2 = st.SIG[(long long)lane * Vcap + s2.y] | st.SIG[(long long)lane * Vcap + s2.z];
+    if (lane == wn) w2 &= ~(3ull << sh);
+    zm = zero_mask(w2, lane, e);
+  }
+  const int c = __popcll(zm);
+  int x = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  const int o2 = r2 >> 1;
+  int j2 = -1;
+  if (o2 >= x - c && o2 < x) {
+    uint64_t mm = zm;
+    for (int q = x - c; q < o2; ++q) mm &= mm - 1;
+    j2 = lane * 32 + (__ffsll((long long)mm) - 1) / 2;
+  }
+  const unsigned owner = __ballot_sync(0xffffffffu, j2 >= 0);
+  if (!owner) return false;
+  j2 = __shfl_sync(0xffffffffu, j2, __ffs(owner) - 1);
+  if (lane == (j2 >> 5)) {
+    const int sj = 2 * (j2 & 31);
+    w2 = (w2 & ~(3ull << sj)) | (((r2 & 1) ? kMinus : kPlus) << sj);
+  }
+  const uint64_t f1 = (lane == wj) ? Fw : s0;
+  return __all_sync(0xffffffffu, lane >= S || f1 == w2);
 }
 
 // ---------------------------------------------------------------------------
@@ -202,6 +350,10 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
   const long long nV = cur->nV_before, nE = cur->nE_before;
   const int G = gridDim.x;
   for (int q = threadIdx.x; q < G; q += kBlock) sm.pref[q] = st.cta_count[q];
+  if (threadIdx.x == 0) {
+    sm.npairs = 0;
+    sm.acc[0] = sm.acc[1] = 0;
+  }
   __syncthreads();
   block_scan_pref(sm, G);
   const long long total = sm.pref[G];
@@ -233,12 +385,12 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
     cur->tsize = tneed;
   }
   const long long Vcap = st.Vcap;
-  const long long chunk = (nE + G - 1) / G;
+  long long chunk, b0, b1;
+  cta_range(nE, chunk, b0, b1);
   const int H = net.w[l + 1];
   ZT* Z = static_cast<ZT*>(st.Z[zb]);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int e = m + n, wn = e >> 5, sh = 2 * (e & 31);
-  uint64_t* s0row = sm.s0row[warp];
   int* zlist = sm.zlist[warp];
   const long long tmask = tneed - 1;
   long long nkeys_w = 0, ndeg_w = 0;
@@ -249,45 +401,76 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
       const int mid = (lo + hi + 1) >> 1;
       if (sm.pref[mid] <= k) lo = mid; else hi = mid - 1;
     }
-    const int32_t ed = st.stage[lo * chunk + (k - sm.pref[lo])];
-    const int32_t u = st.EU[ed], w = st.EW[ed];
-    const bool u_plus = ((st.SIG[(long long)wn * Vcap + u] >> sh) & 3ull) == kPlus;
-    const int32_t p = u_plus ? u : w;   // V+
-    const int32_t q = u_plus ? w : u;   // V-
+    const int4 sg = st.stage[lo * chunk + (k - sm.pref[lo])];
+    const int32_t ed = sg.x, p = sg.y, q = sg.z;  // p: V+, q: V-
     const double a = static_cast<double>(Z[(long long)i * Vcap + p]);
     const double b = static_cast<double>(Z[(long long)i * Vcap + q]);
+    double xp = 0.0, xq = 0.0;
+    if (lane < D) {
+      xp = st.X[(long long)lane * Vcap + p];
+      xq = st.X[(long long)lane * Vcap + q];
+    }
+    uint64_t sp = 0, sq = 0;
+    if (lane < S) {
+      sp = st.SIG[(long long)lane * Vcap + p];
+      sq = st.SIG[(long long)lane * Vcap + q];
+    }
     double t = a / (a - b);
     bool bad = !(a > 0.0 && b < 0.0);
     if (!(t >= 0.0 && t <= 1.0)) { t = t < 0.0 ? 0.0 : 1.0; bad = true; }
     const int32_t v0 = int32_t(nV + k);
-    if (lane < D) {
-      const double xp = st.X[(long long)lane * Vcap + p], xq = st.X[(long long)lane * Vcap + q];
-      st.X[(long long)lane * Vcap + v0] = fma(t, xq - xp, xp);
-    }
+    if (lane < D) st.X[(long long)lane * Vcap + v0] = fma(t, xq - xp, xp);
     const ZT tz = static_cast<ZT>(t);
+    const float* nrl = net.nrm + 3 * net.off[l];
     float amax = 0.f;
-    for (int j = lane; j < H; j += 32) {
-      const ZT zp = Z[(long long)j * Vcap + p], zq = Z[(long long)j * Vcap + q];
-      Z[(long long)j * Vcap + v0] = (j == i) ? ZT(0) : zp + tz * (zq - zp);
-      if (TRACK) amax = fmaxf(amax, fabsf(static_cast<float>(zp)) + fabsf(static_cast<float>(zq)));
+    for (int j0 = 0; j0 < H; j0 += 64) {
+      const int ja = j0 + lane, jb = ja + 32;
+      ZT zpa = ZT(0), zqa = ZT(0), zpb = ZT(0), zqb = ZT(0);
+      if (ja < H) {
+        zpa = Z[(long long)ja * Vcap + p];
+        zqa = Z[(long long)ja * Vcap + q];
+      }
+      if (jb < H) {
+        zpb = Z[(long long)jb * Vcap + p];
+        zqb = Z[(long long)jb * Vcap + q];
+      }
+      const ZT za = (ja == i) ? ZT(0) : zpa + tz * (zqa - zpa);
+      const ZT zb2 = (jb == i) ? ZT(0) : zpb + tz * (zqb - zpb);
+      if (ja < H) Z[(long long)ja * Vcap + v0] = za;
+      if (jb < H) Z[(long long)jb * Vcap + v0] = zb2;
+      if (TRACK) {  // the rounding of z_j, in units of ||W_j||_2
+        if (ja < H) amax = fmaxf(amax, fabsf(static_cast<float>(za)) * nrl[3 * ja + 2]);
+        if (jb < H) amax = fmaxf(amax, fabsf(static_cast<float>(zb2)) * nrl[3 * jb + 2]);
+      }
     }
     if (TRACK) {
       // error estimates: values (rounding of the interpolation) and position
       // (a t computed from values carrying the endpoints' estimates)
       for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-      float dx = 0.f;
-      if (lane < D) dx = fabsf(static_cast<float>(st.X[(long long)lane * Vcap + q] - st.X[(long long)lane * Vcap + p]));
+      float dx = lane < D ? static_cast<float>(fabs(xq - xp)) : 0.f;
       for (int o = 16; o > 0; o >>= 1) dx = fmaxf(dx, __shfl_xor_sync(0xffffffffu, dx, o));
       if (lane == 0) {
-        const float ep = st.esc[p], eq = st.esc[q];
-        st.esc[v0] = fmaxf(ep, eq) + 2.4e-7f * amax;  // 4 * 2^-24
-        st.exc[v0] = fmaxf(st.exc[p], st.exc[q]) + static_cast<float>((ep + eq) / (a - b)) * dx;
+        // rms estimates, independent errors adding in quadrature.  value
+        // scale: the endpoints' scales (the convex combination does not
+        // amplify them) and the interpolation's rounding (u of |z_j|, in units
+        // of ||W_j||_2).
+        // position: the shift along the edge that the errors of a and b cause
+        // in t = a / (a - b), added in quadrature to the endpoints' position
+        // estimates (independent errors; the convex combination does not
+        // amplify the endpoints' own errors).
+        const float rp = st.esc[p], rq = st.esc[q];
+        const float rm = fmaxf(rp, rq), rr = 5.9604645e-8f * amax;
+        st.esc[v0] = sqrtf(rm * rm + rr * rr);
+        const float ep = nrl[3 * i] * rp + 2.9802322e-8f * nrl[3 * i + 1];
+        const float eq = nrl[3 * i] * rq + 2.9802322e-8f * nrl[3 * i + 1];
+        const float shift = static_cast<float>((ep + eq) / (a - b)) * dx;
+        const float xe = fmaxf(st.exc[p], st.exc[q]);
+        st.exc[v0] = sqrtf(xe * xe + shift * shift);
       }
     }
     // sign vector of the new vertex: join of the endpoints, entry n := 0
     uint64_t s0 = 0, zm = 0;
     if (lane < S) {
-      const uint64_t sp = st.SIG[(long long)lane * Vcap + p], sq = st.SIG[(long long)lane * Vcap + q];
       uint64_t conf = ((sp & kEvenBits) & ((sq >> 1) & kEvenBits)) | ((sq & kEvenBits) & ((sp >> 1) & kEvenBits));
       s0 = sp | sq;
       if (lane == wn) {
@@ -296,7 +479,6 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
       }
       if (conf) err_w |= kErrConflict;
       st.SIG[(long long)lane * Vcap + v0] = s0;
-      s0row[lane] = s0;
       zm = zero_mask(s0, lane, e);
     }
     if (lane == 0) {
@@ -332,84 +514,97 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
     for (int o = 16; o > 0; o >>= 1) hb ^= __shfl_xor_sync(0xffffffffu, hb, o);
     __syncwarp();
     if (nz != D - 1) bad = true;
-    // this lane's key: ordinal o = lane / 2 of the zeros, sign + (even) or - (odd)
+    // this lane's key: zero ordinal lane / 2, sign + (even lane) or - (odd)
     const int o = lane >> 1;
     const bool minus = lane & 1;
     const int jz = (nz == D - 1 && o < nz) ? zlist[o] : 0;
     const int wj = jz >> 5, shj = 2 * (jz & 31);
     const uint64_t s0w = __shfl_sync(0xffffffffu, s0, wj);
     const bool has_key = (nz == D - 1) && (o < nz) && !(minus && jz < m);
-    const int nk = __popc(__ballot_sync(0xffffffffu, has_key));
-    nkeys_w += nk;
+    nkeys_w += __popc(__ballot_sync(0xffffffffu, has_key));
     if (bad) ndeg_w += 1;
-    __threadfence();  // publish the new vertex before its keys
+    uint64_t Fw = 0, mine = 0;
+    uint32_t tag = 0;
+    long long slot = 0;
     if (has_key) {
-      const uint64_t Fw = (s0w & ~(3ull << shj)) | ((minus ? kMinus : kPlus) << shj);
+      Fw = (s0w & ~(3ull << shj)) | ((minus ? kMinus : kPlus) << shj);
       const uint64_t h = hb ^ word_hash(wj, s0w) ^ word_hash(wj, Fw);
-      const uint32_t tag = uint32_t(h >> 32);
-      const uint64_t payload = uint64_t(k) * R + uint64_t(lane);
-      const uint64_t mine = (uint64_t(tag) << 32) | payload;
-      long long slot = (long long)(h & (uint64_t)tmask);
-      bool done = false;
-      for (long long probe = 0; probe < tneed; ++probe) {
-        const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(st.table + slot),
-                                       (unsigned long long)kEmpty, (unsigned long long)mine);
-        if (old == kEmpty) { done = true; break; }
-        if (uint32_t(old >> 32) == tag) {
-          __threadfence();
-          const uint64_t pp = old & 0x7fffffffull;
-          const long long k2 = (long long)(pp / R);
-          const int r2 = int(pp % R);
-          const long long v2 = nV + k2;
-          // reconstruct the partner's face and compare word by word
-          const int o2 = r2 >> 1;
-          const bool minus2 = r2 & 1;
-          int seen = 0, j2 = -1;
-          bool equal = true;
-          uint64_t s2[kMaxWords];
-          for (int ww = 0; ww < S; ++ww) {
-            s2[ww] = __ldcg(st.SIG + (long long)ww * Vcap + v2);
-            uint64_t z2 = zero_mask(s2[ww], ww, e);
-            while (z2 && j2 < 0) {
-              const int bit = __ffsll((long long)z2) - 1;
-              if (seen == o2) j2 = ww * 32 + bit / 2;
-              ++seen;
-              z2 &= z2 - 1;
+      tag = uint32_t(h >> 32);
+      mine = (uint64_t(tag) << 32) | (uint64_t(k) * R + uint64_t(lane));
+      slot = (long long)(h & (uint64_t)tmask);
+    }
+    bool active = has_key;
+    long long probes = 0;
+    while (__any_sync(0xffffffffu, active)) {
+      bool cand = false;
+      uint64_t old = 0;
+      if (active) {
+        old = atomicCAS(reinterpret_cast<unsigned long long*>(st.table + slot), (unsigned long long)kEmpty,
+                        (unsigned long long)mine);
+        if (old == kEmpty) {
+          active = false;  // first arrival: the partner will pair with it
+        } else if (uint32_t(old >> 32) == tag) {
+          cand = true;
+        } else {
+          slot = (slot + 1) & tmask;
+          if (++probes > tneed) { err_w |= kErrProbe; active = false; }
+        }
+      }
+      unsigned cm = __ballot_sync(0xffffffffu, cand);
+      while (cm) {
+        const int L = __ffs(cm) - 1;
+        cm &= cm - 1;
+        const uint64_t pp = __shfl_sync(0xffffffffu, old, L) & 0x7fffffffull;
+        const int wjL = __shfl_sync(0xffffffffu, wj, L);
+        const uint64_t FwL = __shfl_sync(0xffffffffu, Fw, L);
+        const bool eq = warp_face_matches(st, sm, G, chunk, (long long)(pp / R), int(pp % R), e, S, s0, wjL, FwL);
+        if (lane == L) {
+          if (eq) {
+            const uint64_t prev = atomicOr(reinterpret_cast<unsigned long long*>(st.table + slot),
+                                           (unsigned long long)kPaired);
+            if (prev & kPaired) {
+              err_w |= kErrPairing;
+            } else {
+              const int v2 = int(nV + (long long)(pp / R));
+              const int slot2 = atomicAdd(&sm.npairs, 1);
+              if (slot2 < kPairCap) {
+                sm.pairs[slot2] = make_int2(v2, v0);
+              } else {
+                const long long idx = atomic_add_ll(&cur->npairs, 1ll);
+                st.EU[nE + total + idx] = v2;
+                st.EW[nE + total + idx] = v0;
+              }
             }
-          }
-          if (j2 < 0) equal = false;
-          for (int ww = 0; ww < S && equal; ++ww) {
-            uint64_t f1 = s0row[ww];
-            if (ww == wj) f1 = Fw;
-            uint64_t f2 = s2[ww];
-            if (ww == (j2 >> 5)) f2 = (f2 & ~(3ull << (2 * (j2 & 31)))) | ((minus2 ? kMinus : kPlus) << (2 * (j2 & 31)));
-            equal = (f1 == f2);
-          }
-          if (equal) {
-            if (old & kPaired) { err_w |= kErrPairing; done = true; break; }
-            const uint64_t prev = atomicCAS(reinterpret_cast<unsigned long long*>(st.table + slot),
-                                            (unsigned long long)old, (unsigned long long)(old | kPaired));
-            if (prev != old) { err_w |= kErrPairing; done = true; break; }
-            const long long idx = atomic_add_ll(&cur->npairs, 1ll);
-            const long long eo = nE + total + idx;
-            st.EU[eo] = int32_t(v2);
-            st.EW[eo] = v0;
-            done = true;
-            break;
+            active = false;
+          } else {
+            slot = (slot + 1) & tmask;
+            if (++probes > tneed) { err_w |= kErrProbe; active = false; }
           }
         }
-        slot = (slot + 1) & tmask;
       }
-      if (!done) err_w |= kErrProbe;
     }
     __syncwarp();
   }
-  if (lane == 0) {
-    if (nkeys_w) atomic_add_ll(&cur->nkeys, nkeys_w);
-    if (ndeg_w) atomic_add_ll(&cur->ndegenerate, ndeg_w);
-  }
   err_w = __reduce_or_sync(0xffffffffu, err_w);
-  if (lane == 0 && err_w) atomicOr(&st.g->error, err_w);
+  if (lane == 0) {
+    if (nkeys_w) atomicAdd(reinterpret_cast<unsigned long long*>(&sm.acc[0]), (unsigned long long)nkeys_w);
+    if (ndeg_w) atomicAdd(reinterpret_cast<unsigned long long*>(&sm.acc[1]), (unsigned long long)ndeg_w);
+    if (err_w) atomicOr(&st.g->error, err_w);
+  }
+  __syncthreads();
+  // this CTA's intersecting edges: one global allocation
+  const int np = sm.npairs < kPairCap ? sm.npairs : kPairCap;
+  if (threadIdx.x == 0) {
+    sm.acc[2] = np ? atomic_add_ll(&cur->npairs, (long long)np) : 0;
+    if (sm.acc[0]) atomic_add_ll(&cur->nkeys, sm.acc[0]);
+    if (sm.acc[1]) atomic_add_ll(&cur->ndegenerate, sm.acc[1]);
+  }
+  __syncthreads();
+  const long long base = nE + total + sm.acc[2];
+  for (int t = threadIdx.x; t < np; t += kBlock) {
+    st.EU[base + t] = sm.pairs[t].x;
+    st.EW[base + t] = sm.pairs[t].y;
+  }
   return false;
 }
 
