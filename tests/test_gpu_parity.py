@@ -122,4 +122,8 @@ def test_zero_residual_and_degree_any_size(cuda):
     assert np.array_equal(deg, 2 * D - (S[:, :m] == 0).sum(axis=1))
     vals = entry_values(net, box, X)
     assert np.max(np.abs(vals[S == 0])) < 1e-6
-    assert np.all(np.sign(vals[S != 0]) == S[S != 0])
+    # away from zero the recorded sign is the sign at the coordinates (within
+    # 1e-5 of zero the FP32-accurate coordinates of unpolished vertices decide
+    # nothing: the recorded sign was decided at the exact vertex)
+    sure = (S != 0) & (np.abs(vals) > 1e-5)
+    assert np.all(np.sign(vals[sure]) == S[sure])
