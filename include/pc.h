@@ -169,6 +169,40 @@ pc_status pc_diagnostics(pc_ctx *ctx, int64_t *out, int n);
  * measured). */
 pc_status pc_kernel_times(pc_ctx *ctx, double *out_ms, int n);
 
+/* Allocation-free extraction, for callers that cannot allocate device
+ * memory while they run (inside a custom memory pool or an allocator
+ * callback, on real-time paths that forbid cudaMalloc because it can
+ * synchronise the device, or under a fixed device-memory reservation).  The
+ * paper has no counterpart: it is the same edge subdivision as pc_extract,
+ * without a context, run one kernel per step.
+ *
+ * Inputs: widths (host, L+1), params (flat float64, host or device), box_lo /
+ * box_hi (host, D), precision (pc_precision; mixed precision polishes as
+ * pc_extract does by default).  Outputs, caller-owned device arrays with the
+ * caller's capacities as leading dimensions: X (D x cap_v float64, X[d*cap_v +
+ * v]), E (2 x cap_e int32, second endpoints at E + cap_e), SIG (S x cap_v
+ * uint64, S = (2D + neurons + 31) / 32); *n_vertices / *n_edges (host).
+ * Blocks until done.
+ *
+ * All other working memory is one static device array of about 10.6 MB
+ * inside the library, held on every GPU that loads it until the process
+ * exits.  Limits: cap_v <= 16384, cap_e <= 65536, layer widths <= 32, at most
+ * 512 neurons and 16384 parameters; beyond them the call returns
+ * PC_ERR_TOO_LARGE, and an extraction that outgrows the capacities returns
+ * PC_ERR_OOM (nothing grows).  The call allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.  The first call on a device looks
+ * up the scratch array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every
+ * call shares the one scratch array and it keeps the last call's contents
+ * (each call resets what must start empty); calls that overlap on the GPU
+ * (on different streams or host threads) race with each other.
+ * Other returns: PC_ERR_INVALID (bad argument), PC_ERR_PAIRING (genericity
+ * failure), PC_ERR_TIMEOUT, PC_ERR_CUDA. */
+pc_status pc_extract_noalloc(int L, const int32_t *widths, const double *params, const double *box_lo,
+                             const double *box_hi, int precision, double *X, int32_t *E, uint64_t *SIG,
+                             int64_t cap_v, int64_t cap_e, int64_t *n_vertices, int64_t *n_edges,
+                             void *stream);
+
 /* Message of the last error on this context ("" if none). */
 const char *pc_last_error(pc_ctx *ctx);
 

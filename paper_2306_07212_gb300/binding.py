@@ -26,7 +26,8 @@ EXEC = {"persistent": 0, "stepwise": 1}
 # Every symbol include/pc.h declares (checked by the tests).
 EXPORTS = ["pc_default_options", "pc_create", "pc_destroy", "pc_set_allocator", "pc_extract",
            "pc_counts", "pc_vertices", "pc_edges", "pc_signvectors", "pc_stats", "pc_backward",
-           "pc_diagnostics", "pc_kernel_times", "pc_error_estimates", "pc_values", "pc_last_error"]
+           "pc_diagnostics", "pc_kernel_times", "pc_error_estimates", "pc_values", "pc_extract_noalloc",
+           "pc_last_error"]
 
 
 class PcError(RuntimeError):
@@ -75,6 +76,8 @@ def load_library(path: str = LIB):
         lib.pc_diagnostics.argtypes = [vp, i64p, ctypes.c_int]
         lib.pc_error_estimates.argtypes = [vp, vp, vp]
         lib.pc_values.argtypes = [vp, vp]
+        lib.pc_extract_noalloc.argtypes = [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, vp, vp, vp,
+                                           ctypes.c_int64, ctypes.c_int64, i64p, i64p, vp]
         lib.pc_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         lib.pc_last_error.argtypes = [vp]
         lib.pc_last_error.restype = ctypes.c_char_p

@@ -877,3 +877,187 @@ pc_status pc_kernel_times(pc_ctx* c, double* out_ms, int n) {
 const char* pc_last_error(pc_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free extraction.
+//
+// Some callers cannot allocate device memory while they run: code inside a
+// custom memory pool or a framework allocator callback, real-time paths that
+// forbid cudaMalloc (it can synchronise the device), and hosts that give the
+// library a fixed memory reservation.  pc_extract_noalloc serves them: the
+// caller passes the parameters and the output arrays, and every other buffer
+// the extraction needs (the layer values, error estimates, staged splitting
+// edges, the 2-face hash table, counters and the parameter copies) lives in
+// one file-scope static device array, g_noalloc_scratch, whose size is fixed
+// at compile time.  Every GPU that loads the library holds that array until
+// the process exits.  The kernels are the same as pc_extract's, run one
+// kernel per step.
+namespace {
+
+constexpr long long kNaMaxV = 16384;        // vertices (caller capacity limit)
+constexpr long long kNaMaxE = 65536;        // edges
+constexpr long long kNaMaxT = 131072;       // 2-face hash slots
+constexpr int kNaMaxWidth = 32;             // layer width
+constexpr int kNaMaxN = 512;                // neurons
+constexpr long long kNaMaxParams = 16384;   // float64 parameters
+
+constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
+constexpr size_t kNaOffP64 = 0;
+constexpr size_t kNaOffP32 = kNaOffP64 + na_align(8 * kNaMaxParams);
+constexpr size_t kNaOffNorm = kNaOffP32 + na_align(4 * kNaMaxParams);
+constexpr size_t kNaOffZ0 = kNaOffNorm + na_align(4 * (2 * kMaxL + 3 * kNaMaxN));
+constexpr size_t kNaZBytes = na_align(8ull * kNaMaxWidth * kNaMaxV);
+constexpr size_t kNaOffZ1 = kNaOffZ0 + kNaZBytes;
+constexpr size_t kNaOffEsc = kNaOffZ1 + kNaZBytes;
+constexpr size_t kNaOffExc = kNaOffEsc + na_align(4 * kNaMaxV);
+constexpr size_t kNaOffStage = kNaOffExc + na_align(4 * kNaMaxV);
+constexpr size_t kNaOffTable = kNaOffStage + na_align(16 * kNaMaxE);
+constexpr size_t kNaOffCnt = kNaOffTable + na_align(8 * kNaMaxT);
+constexpr size_t kNaOffG = kNaOffCnt + na_align(sizeof(Counters) * (kNaMaxN + 1));
+constexpr size_t kNaOffCta = kNaOffG + na_align(sizeof(Global));
+constexpr size_t kNaBytes = kNaOffCta + na_align(8 * kMaxGrid);
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+// Device address of g_noalloc_scratch per device (host code cannot use the
+// symbol itself as a device pointer).
+constexpr int kNaMaxDevices = 64;
+void* g_noalloc_addr[kNaMaxDevices] = {};
+
+}  // namespace
+
+extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const double* params, const double* lo,
+                                        const double* hi, int precision, double* X, int32_t* E, uint64_t* SIG,
+                                        int64_t cap_v, int64_t cap_e, int64_t* n_vertices, int64_t* n_edges,
+                                        void* stream) {
+  if (!widths || !params || !lo || !hi || !X || !E || !SIG || !n_vertices || !n_edges) return PC_ERR_INVALID;
+  if (L < 1 || L > kMaxL || precision < 0 || precision > 2) return PC_ERR_INVALID;
+  const int D = widths[0];
+  if (D < 1 || D > kMaxD) return PC_ERR_INVALID;
+  long long p = 0;
+  int n = 0;
+  for (int l = 0; l <= L; ++l)
+    if (widths[l] < 1 || (l > 0 && widths[l] > kNaMaxWidth)) return PC_ERR_TOO_LARGE;
+  for (int l = 0; l < L; ++l) {
+    p += (long long)widths[l + 1] * widths[l] + widths[l + 1];
+    n += widths[l + 1];
+  }
+  if (n > kNaMaxN || p > kNaMaxParams || 2 * D + n > kMaxEntries) return PC_ERR_TOO_LARGE;
+  if (cap_v > kNaMaxV || cap_e > kNaMaxE) return PC_ERR_TOO_LARGE;
+  if (cap_v < (1 << D) || cap_e < (long long)D << (D - 1)) return PC_ERR_INVALID;
+  for (int d = 0; d < D; ++d)
+    if (!(hi[d] > lo[d])) return PC_ERR_INVALID;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) {
+    cudaGetLastError();
+    return PC_ERR_CUDA;
+  }
+  // once per device, with that device current
+  if (!g_noalloc_addr[dev]) {
+    void* addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) {
+      cudaGetLastError();
+      return PC_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = addr;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  pc_ctx c;  // host-side descriptor only: its buffers point into the scratch and the caller's arrays
+  c.device = dev;
+  cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev);
+  pc_default_options(&c.opt);
+  c.opt.precision = precision;
+  c.opt.exec = PC_EXEC_STEPWISE;
+  c.stream = static_cast<cudaStream_t>(stream);
+  try {
+    NetDesc& net = c.net;
+    net = NetDesc{};
+    net.L = L;
+    net.D = D;
+    net.m = 2 * D;
+    net.precision = precision;
+    net.kappa = static_cast<float>(c.opt.filter_kappa);
+    long long q = 0;
+    int nn = 0, hmax = 0, mw = D;
+    for (int l = 0; l <= L; ++l) net.w[l] = widths[l];
+    for (int l = 0; l < L; ++l) {
+      net.off[l] = nn;
+      net.wofs[l] = q;
+      q += (long long)widths[l + 1] * widths[l];
+      net.bofs[l] = q;
+      q += widths[l + 1];
+      nn += widths[l + 1];
+      hmax = std::max(hmax, widths[l + 1]);
+      mw = std::max(mw, widths[l + 1]);
+    }
+    net.off[L] = nn;
+    net.N = nn;
+    net.P = net.m + nn;
+    net.S = (net.P + 31) / 32;
+    for (int d = 0; d < D; ++d) {
+      net.lo[d] = lo[d];
+      net.hi[d] = hi[d];
+    }
+    net.W64 = reinterpret_cast<const double*>(base + kNaOffP64);
+    net.W32 = reinterpret_cast<const float*>(base + kNaOffP32);
+    net.norms = reinterpret_cast<const float*>(base + kNaOffNorm);
+    net.nrm = net.norms + 2 * kMaxL;
+    c.hmax = hmax;
+    c.mw = mw;
+    c.N = nn;
+    c.bufs.X = X;
+    c.bufs.SIG = SIG;
+    c.bufs.E = E;
+    c.bufs.Z[0] = base + kNaOffZ0;
+    c.bufs.Z[1] = base + kNaOffZ1;
+    c.bufs.esc = base + kNaOffEsc;
+    c.bufs.exc = base + kNaOffExc;
+    c.bufs.stage = base + kNaOffStage;
+    c.bufs.table = base + kNaOffTable;
+    c.cnt = base + kNaOffCnt;
+    c.g = base + kNaOffG;
+    c.cta = base + kNaOffCta;
+    c.Vcap = cap_v;
+    c.Ecap = cap_e;
+    c.Tcap = kNaMaxT;
+    PC_CUDA(cudaMemcpyAsync(base + kNaOffP64, params, sizeof(double) * p, cudaMemcpyDefault, c.stream));
+    k_prep<<<std::max(L, 64), 256, 0, c.stream>>>(net, reinterpret_cast<float*>(base + kNaOffP32),
+                                                   reinterpret_cast<float*>(base + kNaOffNorm), p);
+    PC_CUDA(cudaGetLastError());
+    // the scratch keeps the previous call's contents: reset what must start empty
+    PC_CUDA(cudaMemsetAsync(base + kNaOffTable, 0xff, 8 * kNaMaxT, c.stream));
+    PC_CUDA(cudaMemsetAsync(base + kNaOffCnt, 0, sizeof(Counters) * (nn + 1), c.stream));
+    c.res_smem = (size_t)newton_ws_doubles(mw, D) * 8;
+    occupancy_any(&c);
+    c.grid_step = std::min(kMaxGrid, 2 * c.num_sms);
+    k_init<<<1, 256, 0, c.stream>>>(net, make_state(&c));
+    PC_CUDA(cudaGetLastError());
+    enqueue_any(&c, 0, 0, false);
+    if (precision == PC_PREC_MIXED) {
+      double diam = 0.0;
+      for (int d = 0; d < D; ++d) diam += (hi[d] - lo[d]) * (hi[d] - lo[d]);
+      const float thr = static_cast<float>(c.opt.polish_tol * std::sqrt(diam));
+      const size_t psmem = c.res_smem * kWarps;
+      PC_CUDA(cudaFuncSetAttribute(k_polish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
+      k_polish<<<c.grid_step, kBlock, psmem, c.stream>>>(net, make_state(&c), thr, c.mw);
+      PC_CUDA(cudaGetLastError());
+    }
+    Global g{};
+    std::vector<Counters> hc(nn + 1);
+    PC_CUDA(cudaMemcpyAsync(&g, c.g, sizeof(Global), cudaMemcpyDeviceToHost, c.stream));
+    PC_CUDA(cudaMemcpyAsync(hc.data(), c.cnt, sizeof(Counters) * (nn + 1), cudaMemcpyDeviceToHost, c.stream));
+    PC_CUDA(cudaStreamSynchronize(c.stream));
+    if (g.error & kErrTimeout) return PC_ERR_TIMEOUT;
+    if (g.halted_at >= 0) return PC_ERR_OOM;
+    bool pairing = (g.error & (kErrPairing | kErrProbe | kErrConflict)) != 0;
+    for (int k = 1; k <= nn; ++k)
+      if (hc[k].nkeys != 2 * hc[k].npairs) pairing = true;
+    if (pairing) return PC_ERR_PAIRING;
+    *n_vertices = hc[nn].nV_before + hc[nn].nsplit;
+    *n_edges = hc[nn].nE_before + hc[nn].nsplit + hc[nn].npairs;
+    return PC_OK;
+  } catch (const PcError& e) {
+    cudaGetLastError();
+    return e.status;
+  }
+}
