@@ -132,8 +132,8 @@ __global__ void __launch_bounds__(128) k_gemm_simt(NetDesc net, State st, int l)
   }
   __syncthreads();
   const long long Vcap = st.Vcap;
-  ZT* Zout = static_cast<ZT*>(st.Z[l & 1]);
-  const ZT* Zin = static_cast<const ZT*>(st.Z[(l + 1) & 1]);
+  ZT* Zout = static_cast<ZT*>(st.Z[l]);
+  const ZT* Zin = static_cast<const ZT*>(st.Z[l > 0 ? l - 1 : 0]);
   const int ebase = net.m + (l > 0 ? net.off[l - 1] : 0);
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nV;
        v += (long long)gridDim.x * blockDim.x) {
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_classify(NetDesc net, State st, i
   extern __shared__ double dsm[];
   __shared__ Smem sm;
   if (stopped(st)) return;
-  phase_classify<ZT, MIXED>(net, st, l & 1, l, i, net.off[l] + i, sm, dsm, mw);
+  phase_classify<ZT, MIXED>(net, st, l, l, i, net.off[l] + i, sm, dsm, mw);
 }
 
 __global__ void __launch_bounds__(kBlock) k_reclassify(NetDesc net, State st, int l, int i) {
@@ -213,7 +213,7 @@ template <typename ZT, bool MIXED>
 __global__ void __launch_bounds__(kBlock, 2) k_split(NetDesc net, State st, int l, int i) {
   __shared__ Smem sm;
   if (stopped(st)) return;
-  phase_split<ZT, MIXED>(net, st, l & 1, l, i, net.off[l] + i, sm);
+  phase_split<ZT, MIXED>(net, st, l, l, i, net.off[l] + i, sm);
 }
 
 template <typename ZT, bool MIXED>
@@ -225,13 +225,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_layer(NetDesc net, State st, int 
   const int H = net.w[l + 1];
   for (int i = i_begin; i < H; ++i) {
     const int n = net.off[l] + i;
-    phase_classify<ZT, MIXED>(net, st, l & 1, l, i, n, sm, dsm, mw);
+    phase_classify<ZT, MIXED>(net, st, l, l, i, n, sm, dsm, mw);
     if (!grid_barrier(st.g, passed)) return;
     if (MIXED && *(volatile int*)&st.g->flip_at == n) {
       phase_reclassify(net, st, n, sm);
       if (!grid_barrier(st.g, passed)) return;
     }
-    if (phase_split<ZT, MIXED>(net, st, l & 1, l, i, n, sm)) return;
+    if (phase_split<ZT, MIXED>(net, st, l, l, i, n, sm)) return;
     if (!grid_barrier(st.g, passed)) return;
   }
 }
@@ -327,8 +327,8 @@ static void realloc_state(pc_ctx* c, long long V, long long E, long long T, bool
     if (!p) throw PcError(PC_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
   };
   A(nb.X, sizeof(double) * D * V);
-  A(nb.Z[0], zs * Hm * V);
-  A(nb.Z[1], zs * Hm * V);
+  nb.nz = c->opt.keep_tape ? c->net.L : 2;
+  for (int k = 0; k < nb.nz; ++k) A(nb.Z[k], zs * Hm * V);
   A(nb.esc, sizeof(float) * V);
   A(nb.exc, sizeof(float) * V);
   A(nb.SIG, sizeof(uint64_t) * S * V);
@@ -347,8 +347,7 @@ static void realloc_state(pc_ctx* c, long long V, long long E, long long T, bool
       if (rows && width) PC_CUDA(cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, cudaMemcpyDeviceToDevice, c->stream));
     };
     cp2(nb.X, 8 * V, ob.X, 8 * oV, 8 * nV, D);
-    cp2(nb.Z[0], zs * V, ob.Z[0], zs * oV, zs * nV, Hm);
-    cp2(nb.Z[1], zs * V, ob.Z[1], zs * oV, zs * nV, Hm);
+    for (int k = 0; k < nb.nz && k < ob.nz; ++k) cp2(nb.Z[k], zs * V, ob.Z[k], zs * oV, zs * nV, Hm);
     cp2(nb.esc, 4 * V, ob.esc, 4 * oV, 4 * nV, 1);
     cp2(nb.exc, 4 * V, ob.exc, 4 * oV, 4 * nV, 1);
     cp2(nb.SIG, 8 * V, ob.SIG, 8 * oV, 8 * nV, S);
@@ -383,14 +382,16 @@ static void ensure_fixed(pc_ctx* c, int N) {
   }
 }
 
+static State make_state(pc_ctx* c);
+State pc_make_state(pc_ctx* c) { return make_state(c); }
+
 static State make_state(pc_ctx* c) {
   State s{};
   s.Vcap = c->Vcap;
   s.Ecap = c->Ecap;
   s.Tcap = c->Tcap;
   s.X = static_cast<double*>(c->bufs.X);
-  s.Z[0] = c->bufs.Z[0];
-  s.Z[1] = c->bufs.Z[1];
+  for (int l = 0; l < kMaxL; ++l) s.Z[l] = c->bufs.Z[c->bufs.nz > 2 ? (l < c->bufs.nz ? l : 0) : (l & 1)];
   s.esc = static_cast<float*>(c->bufs.esc);
   s.exc = static_cast<float*>(c->bufs.exc);
   s.SIG = static_cast<uint64_t*>(c->bufs.SIG);
@@ -574,7 +575,8 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   ensure_fixed(c, n);
   const size_t zs = zsize_of(net.precision);
   const bool reshape = !c->bufs.X || c->shape_D != D || c->shape_S < net.S || c->shape_H < hmax ||
-                       c->shape_zs != zs || c->shape_tape != c->opt.keep_tape;
+                       c->shape_zs != zs || c->shape_tape != c->opt.keep_tape ||
+                       (c->opt.keep_tape && c->bufs.nz < L);
   if (reshape) {
     long long V = std::max<long long>(c->Vcap, std::max<long long>(c->opt.init_vcap, 1 << 14));
     long long E = std::max<long long>(c->Ecap, std::max<long long>(c->opt.init_ecap, (long long)D * V));
@@ -685,8 +687,8 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
 
 void StateBufs::release(pc_ctx* c) {
   ctx_free(c, X);
-  ctx_free(c, Z[0]);
-  ctx_free(c, Z[1]);
+  for (int k = 0; k < nz; ++k) ctx_free(c, Z[k]);
+  nz = 0;
   ctx_free(c, esc);
   ctx_free(c, exc);
   ctx_free(c, SIG);
@@ -833,7 +835,7 @@ pc_status pc_values(pc_ctx* c, void* out) {
   if (!c) return PC_ERR_INVALID;
   if (!c->have_result) return c->fail(PC_ERR_INVALID, "no extraction result");
   const int L = c->net.L;
-  return copy_rows(c, out, c->bufs.Z[(L - 1) & 1], zsize_of(c->net.precision), c->Vcap, c->nV, c->net.w[L]);
+  return copy_rows(c, out, pc_make_state(c).Z[L - 1], zsize_of(c->net.precision), c->Vcap, c->nV, c->net.w[L]);
 }
 
 pc_status pc_error_estimates(pc_ctx* c, float* value_scale, float* coord_rms) {
@@ -1010,6 +1012,7 @@ extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const doub
     c.bufs.E = E;
     c.bufs.Z[0] = base + kNaOffZ0;
     c.bufs.Z[1] = base + kNaOffZ1;
+    c.bufs.nz = 2;
     c.bufs.esc = base + kNaOffEsc;
     c.bufs.exc = base + kNaOffExc;
     c.bufs.stage = base + kNaOffStage;

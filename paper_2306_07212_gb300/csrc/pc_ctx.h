@@ -15,6 +15,7 @@ struct pc_ctx;
 
 void* ctx_alloc(pc_ctx* c, size_t bytes);
 void ctx_free(pc_ctx* c, void*& p);
+pc::State pc_make_state(pc_ctx* c);
 
 struct PcError : std::runtime_error {
   pc_status status;
@@ -23,7 +24,8 @@ struct PcError : std::runtime_error {
 
 struct StateBufs {
   void* X = nullptr;
-  void* Z[2] = {nullptr, nullptr};
+  void* Z[pc::kMaxL] = {};   // nz value buffers (2, or one per layer with the tape)
+  int nz = 0;
   void* esc = nullptr;
   void* exc = nullptr;
   void* SIG = nullptr;

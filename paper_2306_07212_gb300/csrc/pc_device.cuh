@@ -4,7 +4,8 @@
 //   X     [D][Vcap]   float64 vertex coordinates
 //   Z     [H][Vcap]   current-layer pre-activations (float32, or float64 in
 //                     FP64 mode), neuron-major so one neuron's pass reads a
-//                     contiguous row; two buffers ping-pong across layers
+//                     contiguous row; two buffers ping-pong across layers, or
+//                     one per layer when the interpolation tape is kept
 //   esc   [Vcap]      float32 error scale rho of the vertex's FP32 Z column:
 //                     the rms error of z_j is about ||W_j||_2 rho + u/2 |b_j|
 //                     (FP32 and mixed precision)
@@ -87,7 +88,7 @@ struct Global {
 struct State {
   long long Vcap, Ecap, Tcap;
   double* X;
-  void* Z[2];
+  void* Z[kMaxL];        // values of layer l (ping-pong pair unless the tape keeps every layer)
   float* esc;            // FP32 value error estimate per vertex
   float* exc;            // coordinate error estimate per vertex (absolute)
   uint64_t* SIG;
