@@ -237,10 +237,43 @@ def run_ours(args, rank, world, local_rank):
                "step_ms_median": round(statistics.median(step_ms), 4)}
         if cpu:
             out["cpu_baseline"] = cpu
+        if args.serve_requests > 0 and world == 1:
+            lim = 1 << 30
+            out["serving"] = {
+                "workload": f"Poisson stream, mean 200 req/s, {args.serve_requests} requests, D in {{2,3,4}}, "
+                            "depth 2-6, width in {16,32,64,128}, He-normal FP32 weights, mixed precision; "
+                            f"requests estimated above {lim >> 30} GiB rejected",
+                "batched": run_serving(args.serve_requests, 8, lim),
+                "plain": run_serving(args.serve_requests, 1, lim)}
     ex.close()
     if dist:
         dist.destroy_process_group()
     return out
+
+
+def run_serving(n_requests: int, slots: int, request_max_bytes: int):
+    """Poisson stream of extraction requests (serving workload); latencies in ms."""
+    import numpy as np
+    from paper_2306_07212_gb300 import binding, workloads
+    reqs = workloads.serving_stream(n_requests)
+    with binding.Server(max_slots=slots, request_max_bytes=request_max_bytes, mem_budget_bytes=48 << 30) as srv:
+        t0 = time.perf_counter()
+        ids = []
+        for r in reqs:
+            dt = r.arrival_s - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit(r.net, r.box))
+        srv.wait_all(1800)
+        res = [srv.poll(i)[1] for i in ids]
+    ok = [r for r in res if r.status == 0]
+    lat = np.array([r.finish_s - r.arrival_s for r in ok]) * 1e3
+    span = max(r.finish_s for r in ok) - min(r.arrival_s for r in res)
+    ve = sum(r.n_vertices + r.n_edges for r in ok)
+    return {"slots": slots, "p50_ms": round(float(np.percentile(lat, 50)), 2),
+            "p99_ms": round(float(np.percentile(lat, 99)), 2), "req_per_s": round(len(ok) / span, 2),
+            "ve_per_s": round(ve / span, 1), "completed": len(ok),
+            "rejected": sum(r.status == 6 for r in res), "failed": sum(r.status not in (0, 6) for r in res)}
 
 
 def cpu_baseline(net, box):
@@ -286,6 +319,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
     ap.add_argument("--execution", default="persistent", choices=["persistent", "stepwise"])
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving stream to replay (0 = skip the serving measurement)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -169,6 +169,68 @@ pc_status pc_diagnostics(pc_ctx *ctx, int64_t *out, int n);
  * measured). */
 pc_status pc_kernel_times(pc_ctx *ctx, double *out_ms, int n);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a persistent request loop around pc_extract (no counterpart in the
+ * paper).  Requests arrive at any time (pc_server_submit copies the inputs
+ * and returns at once).  A request whose memory estimate exceeds
+ * request_max_bytes is rejected with PC_ERR_TOO_LARGE; the others queue in
+ * FIFO order.  max_slots worker threads each own one context and one CUDA
+ * stream; a free worker admits the head of the queue once the running
+ * requests' estimates plus its own fit mem_budget_bytes, so requests that
+ * arrive while others run are admitted as slots and memory free up and their
+ * kernels overlap on the device; each context grows its arrays on overflow.
+ * max_slots = 1 is the plain per-request path (FIFO, one at a time, same
+ * kernels).  Times are seconds on the server's clock (since creation).
+ * Thread-safe: submit / poll / wait_all may be called from any thread. */
+typedef struct pc_server pc_server;
+
+typedef struct {
+  int max_slots;               /* concurrent requests (1 = plain FIFO path) */
+  int precision;               /* pc_precision of every request */
+  int exec;                    /* pc_exec of every request */
+  int polish;                  /* pc_options.polish of every request */
+  int keep_outputs;            /* keep each result's arrays in host memory */
+  int64_t mem_budget_bytes;    /* admission limit on the summed estimates */
+  int64_t request_max_bytes;   /* larger estimates are rejected */
+} pc_server_options;
+
+typedef struct {
+  pc_status status;            /* PC_PENDING until finished */
+  int64_t n_vertices, n_edges;
+  double arrival_s, start_s, finish_s;
+  int64_t est_bytes;           /* admission estimate (pc_estimate_bytes) */
+  int slot;                    /* worker that ran it (-1 if rejected) */
+  int64_t held_bytes;          /* device bytes its worker's context held after it */
+} pc_result;
+
+/* Device-memory estimate of one extraction: vertices ~ 1.2 N^D / D! for
+ * generic ReLU nets with N neurons (the measured range is 0.4 - 1.2), edges ~
+ * D x vertices, doubled for capacity growth.  -1 on bad input. */
+int64_t pc_estimate_bytes(int L, const int32_t *widths);
+/* Defaults: 8 slots, mixed precision, stepwise execution, no polish, 64 GiB
+ * budget, 8 GiB per request. */
+void pc_server_default_options(pc_server_options *opt);
+pc_status pc_server_create(pc_server **out, int device, const pc_server_options *opt);
+/* Inputs are host arrays (copied): widths L+1, params flat float64, box D. */
+pc_status pc_server_submit(pc_server *s, int L, const int32_t *widths, const double *params,
+                           const double *box_lo, const double *box_hi, uint64_t *id);
+/* PC_OK with the final result, PC_PENDING while queued or running. */
+pc_status pc_server_poll(pc_server *s, uint64_t id, pc_result *out);
+/* Blocks until no request is queued or running (PC_ERR_TIMEOUT after
+ * timeout_s seconds). */
+pc_status pc_server_wait_all(pc_server *s, double timeout_s);
+/* keep_outputs: copies a finished request's arrays to host memory: X (D x nV,
+ * row d at X + d * nV), E (2 x nE), SIG (S x nV); any may be NULL. */
+pc_status pc_server_outputs(pc_server *s, uint64_t id, double *X, int32_t *E, uint64_t *SIG);
+/* Error message of a failed request ("" if none); valid until release. */
+const char *pc_server_error(pc_server *s, uint64_t id);
+/* Forgets a finished request (frees its kept outputs). */
+pc_status pc_server_release(pc_server *s, uint64_t id);
+/* Peak and current summed estimates of admitted requests. */
+pc_status pc_server_stats(pc_server *s, int64_t *peak_bytes, int64_t *in_use_bytes);
+/* Stops the workers (queued requests are dropped) and frees everything. */
+pc_status pc_server_destroy(pc_server *s);
+
 /* Allocation-free extraction, for callers that cannot allocate device
  * memory while they run (inside a custom memory pool or an allocator
  * callback, on real-time paths that forbid cudaMalloc because it can

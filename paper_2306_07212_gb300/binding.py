@@ -27,13 +27,27 @@ EXEC = {"persistent": 0, "stepwise": 1}
 EXPORTS = ["pc_default_options", "pc_create", "pc_destroy", "pc_set_allocator", "pc_extract",
            "pc_counts", "pc_vertices", "pc_edges", "pc_signvectors", "pc_stats", "pc_backward",
            "pc_diagnostics", "pc_kernel_times", "pc_error_estimates", "pc_values", "pc_extract_noalloc",
-           "pc_last_error"]
+           "pc_estimate_bytes", "pc_server_default_options", "pc_server_create", "pc_server_submit",
+           "pc_server_poll", "pc_server_error", "pc_server_wait_all", "pc_server_outputs", "pc_server_release", "pc_server_stats",
+           "pc_server_destroy", "pc_last_error"]
 
 
 class PcError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
         self.status = status
+
+
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int), ("precision", ctypes.c_int), ("exec", ctypes.c_int),
+                ("polish", ctypes.c_int), ("keep_outputs", ctypes.c_int),
+                ("mem_budget_bytes", ctypes.c_int64), ("request_max_bytes", ctypes.c_int64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("n_vertices", ctypes.c_int64), ("n_edges", ctypes.c_int64),
+                ("arrival_s", ctypes.c_double), ("start_s", ctypes.c_double), ("finish_s", ctypes.c_double),
+                ("est_bytes", ctypes.c_int64), ("slot", ctypes.c_int), ("held_bytes", ctypes.c_int64)]
 
 
 class Options(ctypes.Structure):
@@ -76,13 +90,28 @@ def load_library(path: str = LIB):
         lib.pc_diagnostics.argtypes = [vp, i64p, ctypes.c_int]
         lib.pc_error_estimates.argtypes = [vp, vp, vp]
         lib.pc_values.argtypes = [vp, vp]
+        lib.pc_estimate_bytes.argtypes = [ctypes.c_int, vp]
+        lib.pc_estimate_bytes.restype = ctypes.c_int64
+        lib.pc_server_default_options.argtypes = [ctypes.POINTER(ServerOptions)]
+        lib.pc_server_default_options.restype = None
+        lib.pc_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ServerOptions)]
+        lib.pc_server_submit.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+        lib.pc_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result)]
+        lib.pc_server_wait_all.argtypes = [vp, ctypes.c_double]
+        lib.pc_server_error.argtypes = [vp, ctypes.c_uint64]
+        lib.pc_server_error.restype = ctypes.c_char_p
+        lib.pc_server_outputs.argtypes = [vp, ctypes.c_uint64, vp, vp, vp]
+        lib.pc_server_release.argtypes = [vp, ctypes.c_uint64]
+        lib.pc_server_stats.argtypes = [vp, i64p, i64p]
+        lib.pc_server_destroy.argtypes = [vp]
         lib.pc_extract_noalloc.argtypes = [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, vp, vp, vp,
                                            ctypes.c_int64, ctypes.c_int64, i64p, i64p, vp]
         lib.pc_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         lib.pc_last_error.argtypes = [vp]
         lib.pc_last_error.restype = ctypes.c_char_p
         for f in EXPORTS:
-            if f not in ("pc_default_options", "pc_last_error"):
+            if f not in ("pc_default_options", "pc_last_error", "pc_estimate_bytes", "pc_server_default_options",
+                         "pc_server_error"):
                 getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -282,3 +311,90 @@ class Extractor:
     def backward(self, grad_x, grad_params, stream=None) -> None:
         """pc_backward: grad_x (D, nV) float64, grad_params flat float64 (host or device)."""
         self._check(self._lib.pc_backward(self._ctx, _addr(grad_x), _addr(grad_params), _stream_handle(stream)))
+
+
+class Server:
+    """The request loop of pc_server_*: submit extraction requests at any time,
+    poll or wait for their results (latencies on the server's clock)."""
+
+    def __init__(self, device: int = 0, max_slots: int = 8, precision: str = "mixed", execution: str = "stepwise",
+                 polish: int = 0, keep_outputs: bool = False, mem_budget_bytes: int = 64 << 30,
+                 request_max_bytes: int = 8 << 30):
+        self._lib = load_library()
+        o = ServerOptions()
+        self._lib.pc_server_default_options(ctypes.byref(o))
+        o.max_slots, o.precision, o.exec = max_slots, PRECISION[precision], EXEC[execution]
+        o.polish, o.keep_outputs = int(polish), int(keep_outputs)
+        o.mem_budget_bytes, o.request_max_bytes = int(mem_budget_bytes), int(request_max_bytes)
+        self._s = ctypes.c_void_p()
+        st = self._lib.pc_server_create(ctypes.byref(self._s), device, ctypes.byref(o))
+        if st != PC_OK:
+            raise PcError(st, "pc_server_create failed")
+        self._nets = {}
+
+    def submit(self, net, box) -> int:
+        widths = np.ascontiguousarray(net.widths, np.int32)
+        params = np.ascontiguousarray(net.flat_params(), np.float64)
+        lo = np.ascontiguousarray(box.lo, np.float64)
+        hi = np.ascontiguousarray(box.hi, np.float64)
+        rid = ctypes.c_uint64()
+        st = self._lib.pc_server_submit(self._s, len(net.widths) - 1, _addr(widths), _addr(params), _addr(lo),
+                                        _addr(hi), ctypes.byref(rid))
+        if st != PC_OK:
+            raise PcError(st, "pc_server_submit failed")
+        self._nets[rid.value] = net
+        return rid.value
+
+    def poll(self, rid: int):
+        r = Result()
+        st = self._lib.pc_server_poll(self._s, rid, ctypes.byref(r))
+        return st, r
+
+    def error(self, rid: int) -> str:
+        return self._lib.pc_server_error(self._s, rid).decode()
+
+    def wait_all(self, timeout_s: float = 600.0):
+        st = self._lib.pc_server_wait_all(self._s, float(timeout_s))
+        if st != PC_OK:
+            raise PcError(st, "requests still pending")
+
+    def outputs(self, rid: int):
+        """(X (nV, D), S (S, nV) uint64, E (nE, 2)) of a finished request (keep_outputs)."""
+        st, r = self.poll(rid)
+        net = self._nets[rid]
+        D = net.D
+        S = (2 * D + net.n_neurons + 31) // 32
+        X = np.empty((D, r.n_vertices), np.float64)
+        E = np.empty((2, r.n_edges), np.int32)
+        SIG = np.empty((S, r.n_vertices), np.uint64)
+        st = self._lib.pc_server_outputs(self._s, rid, _addr(X), _addr(E), _addr(SIG))
+        if st != PC_OK:
+            raise PcError(st, "no outputs for this request")
+        return X.T, SIG, np.ascontiguousarray(E.T)
+
+    def stats(self):
+        peak, cur = ctypes.c_int64(), ctypes.c_int64()
+        self._lib.pc_server_stats(self._s, ctypes.byref(peak), ctypes.byref(cur))
+        return {"peak_bytes": peak.value, "in_use_bytes": cur.value}
+
+    def close(self):
+        if getattr(self, "_s", None) and self._s.value:
+            self._lib.pc_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def estimate_bytes(net) -> int:
+    w = np.ascontiguousarray(net.widths, np.int32)
+    return int(load_library().pc_estimate_bytes(len(net.widths) - 1, _addr(w)))

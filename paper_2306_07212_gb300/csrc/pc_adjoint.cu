@@ -172,14 +172,13 @@ static void run_backward(pc_ctx* c, const State& st, float* xbar, float* zb[2], 
       if (cnt <= 0) continue;
       const int blocks = int(std::min<long long>((cnt + 7) / 8, 4096));
       k_adj_split<ZT><<<blocks, 256, 0, c->stream>>>(net, st, xbar, zl, l, i, vb, cnt);
+      if (cudaPeekAtLastError() != cudaSuccess) return;
     }
     const Counters& s0 = hc[net.off[l]];
     const long long nVl = s0.nV_before + s0.nsplit;
     const int H = net.w[l + 1], K = net.w[l];
     const int gy = (H * K + 512 * 32 - 1) / (512 * 32);
-    const size_t smem = sizeof(float) * (H + K) * 32;
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_adj_wgrad<ZT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sizeof(float) * (H + K) * 32;  // <= kAdjSmemMax (widths <= 256)
     const int gx = int(std::max<long long>(1, std::min<long long>((nVl + 31) / 32, 2 * c->num_sms)));
     k_adj_wgrad<ZT><<<dim3(gx, gy), 512, smem, c->stream>>>(net, st, zl, gW, l, nVl);
     if (l > 0) {
@@ -189,9 +188,16 @@ static void run_backward(pc_ctx* c, const State& st, float* xbar, float* zb[2], 
   }
 }
 
+constexpr int kAdjSmemMax = sizeof(float) * 2 * kMaxWidth * 32;
+
 }  // namespace pc
 
 using namespace pc;
+
+void pc_adjoint_set_attributes() {
+  cudaFuncSetAttribute(k_adj_wgrad<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmemMax);
+  cudaFuncSetAttribute(k_adj_wgrad<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmemMax);
+}
 
 extern "C" pc_status pc_backward(pc_ctx* c, const double* grad_x, double* grad_params, void* stream) {
   if (!c || !grad_x || !grad_params) return PC_ERR_INVALID;

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -109,9 +110,13 @@ template <typename ZT, bool MIXED>
 __global__ void __launch_bounds__(128) k_gemm_simt(NetDesc net, State st, int l) {
   constexpr int TJ = 16;
   constexpr bool TRACK = sizeof(ZT) == 4;
-  if (st.g->halted_at >= 0 || (st.g->error & kErrTimeout)) return;
+  if (st.g->halted_at >= 0 || (st.g->error & kErrFatal)) return;
   const Counters* c = st.cnt + net.off[l];
   const long long nV = c->nV_before + c->nsplit;
+  if (nV < 0 || nV > st.Vcap) {
+    if (threadIdx.x == 0) atomicOr(&st.g->error, kErrCorrupt);
+    return;
+  }
   const int H = net.w[l + 1], K = net.w[l];
   const int j0 = blockIdx.y * TJ;
   __shared__ ZT Ws[TJ][kMaxWidth + 1];
@@ -190,7 +195,7 @@ __global__ void __launch_bounds__(128) k_gemm_simt(NetDesc net, State st, int l)
 // Neuron phases: stepwise kernels and the persistent per-layer kernel.
 
 __device__ __forceinline__ bool stopped(const State& st) {
-  return st.g->halted_at >= 0 || (st.g->error & kErrTimeout);
+  return st.g->halted_at >= 0 || (*(volatile int*)&st.g->error & kErrFatal);
 }
 
 template <typename ZT, bool MIXED>
@@ -226,13 +231,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_layer(NetDesc net, State st, int 
   for (int i = i_begin; i < H; ++i) {
     const int n = net.off[l] + i;
     phase_classify<ZT, MIXED>(net, st, l, l, i, n, sm, dsm, mw);
-    if (!grid_barrier(st.g, passed)) return;
+    if (!grid_barrier(st.g, passed) || stopped(st)) return;
     if (MIXED && *(volatile int*)&st.g->flip_at == n) {
       phase_reclassify(net, st, n, sm);
       if (!grid_barrier(st.g, passed)) return;
     }
     if (phase_split<ZT, MIXED>(net, st, l, l, i, n, sm)) return;
-    if (!grid_barrier(st.g, passed)) return;
+    if (!grid_barrier(st.g, passed) || stopped(st)) return;
   }
 }
 
@@ -241,6 +246,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_layer(NetDesc net, State st, int 
 // on its D zero entries (all entries are processed at this point).  One warp
 // per vertex; vertices are dealt to warps round-robin.
 __global__ void __launch_bounds__(kBlock) k_polish(NetDesc net, State st, float thr, int mw) {
+  // blockDim.x = 32 x (warps whose workspace fits kPolishSmemMax)
   extern __shared__ double dsm[];
   __shared__ int zl[kWarps][kMaxD + 2];
   __shared__ NewtonOut nout[kWarps];
@@ -251,8 +257,9 @@ __global__ void __launch_bounds__(kBlock) k_polish(NetDesc net, State st, float 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* ws = dsm + (long long)warp * newton_ws_doubles(mw, net.D);
   long long npol = 0;
-  const long long nwarps = (long long)gridDim.x * kWarps;
-  for (long long base = ((long long)blockIdx.x * kWarps + warp) * 32; base < nV; base += nwarps * 32) {
+  const int wpc = blockDim.x >> 5;
+  const long long nwarps = (long long)gridDim.x * wpc;
+  for (long long base = ((long long)blockIdx.x * wpc + warp) * 32; base < nV; base += nwarps * 32) {
     const long long v = base + lane;
     unsigned flag = __ballot_sync(0xffffffffu, v < nV && !(st.exc[v] <= thr));
     while (flag) {
@@ -318,16 +325,22 @@ void ctx_free(pc_ctx* c, void*& p) {
 static size_t zsize_of(int prec) { return prec == PC_PREC_FP64 ? 8 : 4; }
 
 // (Re)allocates the state for capacities (V, E, T, tape); copies live data.
+// Rows come from the context's recorded buffer shape (set when the buffers
+// are (re)shaped), which covers every network that runs without reshaping,
+// not from the current network (a later, wider one would overrun them).
 static void realloc_state(pc_ctx* c, long long V, long long E, long long T, bool copy) {
-  const int D = c->net.D, S = c->net.S, Hm = c->hmax;
-  const size_t zs = zsize_of(c->net.precision);
+  const int D = c->shape_D, S = c->shape_S, Hm = c->shape_H;
+  const size_t zs = c->shape_zs;
   StateBufs nb;
   auto A = [&](void*& p, size_t bytes) {
     p = ctx_alloc(c, bytes);
-    if (!p) throw PcError(PC_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    if (!p) {
+      nb.release(c);  // nothing half-built survives; the live buffers are untouched
+      throw PcError(PC_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
   };
   A(nb.X, sizeof(double) * D * V);
-  nb.nz = c->opt.keep_tape ? c->net.L : 2;
+  nb.nz = c->shape_tape ? c->shape_nz : 2;
   for (int k = 0; k < nb.nz; ++k) A(nb.Z[k], zs * Hm * V);
   A(nb.esc, sizeof(float) * V);
   A(nb.exc, sizeof(float) * V);
@@ -364,21 +377,41 @@ static void realloc_state(pc_ctx* c, long long V, long long E, long long T, bool
   c->Tcap = T;
 }
 
+// Counters, status block and per-CTA counts.  A failed allocation leaves the
+// context without these buffers (capacity 0), never with a stale capacity.
 static void ensure_fixed(pc_ctx* c, int N) {
   const size_t cnt_bytes = sizeof(Counters) * (N + 1);
-  if (c->cnt_slots < N + 1) {
+  if (c->cnt_slots < N + 1 || !c->cnt || !c->h_cnt) {
+    c->cnt_slots = 0;
     ctx_free(c, c->cnt);
+    if (c->h_cnt) cudaFreeHost(c->h_cnt);
+    c->h_cnt = nullptr;
     c->cnt = ctx_alloc(c, cnt_bytes);
     if (!c->cnt) throw PcError(PC_ERR_OOM, "counter allocation failed");
-    if (c->h_cnt) cudaFreeHost(c->h_cnt);
-    PC_CUDA(cudaMallocHost(&c->h_cnt, cnt_bytes));
+    if (cudaMallocHost(&c->h_cnt, cnt_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      c->h_cnt = nullptr;
+      throw PcError(PC_ERR_OOM, "pinned counter allocation failed");
+    }
     c->cnt_slots = N + 1;
   }
-  if (!c->g) {
+  if (!c->g || !c->cta || !c->h_g) {
+    ctx_free(c, c->g);
+    ctx_free(c, c->cta);
     c->g = ctx_alloc(c, sizeof(Global));
     c->cta = ctx_alloc(c, sizeof(long long) * kMaxGrid);
-    if (!c->g || !c->cta) throw PcError(PC_ERR_OOM, "allocation failed");
-    PC_CUDA(cudaMallocHost(&c->h_g, sizeof(Global)));
+    if (!c->g || !c->cta) {
+      ctx_free(c, c->g);
+      ctx_free(c, c->cta);
+      throw PcError(PC_ERR_OOM, "status allocation failed");
+    }
+    PC_CUDA(cudaMemsetAsync(c->cta, 0, sizeof(long long) * kMaxGrid, c->stream));
+    if (!c->h_g && cudaMallocHost(&c->h_g, sizeof(Global)) != cudaSuccess) {
+      cudaGetLastError();
+      c->h_g = nullptr;
+      ctx_free(c, c->g);
+      throw PcError(PC_ERR_OOM, "pinned status allocation failed");
+    }
   }
 }
 
@@ -457,21 +490,21 @@ struct Kernels {
     } else {
       for (int i = i_begin; i < H; ++i) {
         k_classify<ZT, MIXED><<<c->grid_step, kBlock, c->res_smem, c->stream>>>(c->net, st, l, i, c->mw);
+        PC_CUDA(cudaGetLastError());
         c->launches += 1;
         if (MIXED) {
           k_reclassify<<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l, i);
+          PC_CUDA(cudaGetLastError());
           c->launches += 1;
         }
         k_split<ZT, MIXED><<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l, i);
+        PC_CUDA(cudaGetLastError());
         c->launches += 1;
       }
-      PC_CUDA(cudaGetLastError());
     }
   }
   static int occupancy(pc_ctx* c) {
     int nb = 0;
-    PC_CUDA(cudaFuncSetAttribute(k_layer<ZT, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->res_smem));
-    PC_CUDA(cudaFuncSetAttribute(k_classify<ZT, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->res_smem));
     PC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_layer<ZT, MIXED>, kBlock, c->res_smem));
     return nb;
   }
@@ -552,14 +585,21 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
 
   // parameters: device copies in float64 and float32, per-layer norms
   const size_t pbytes = sizeof(double) * p;
-  if (c->params_cap < p || c->norms_cap < n) {
+  if (c->params_cap < p || c->norms_cap < n || !c->params64 || !c->params32 || !c->norms) {
+    c->params_cap = 0;
+    c->norms_cap = 0;
     ctx_free(c, c->params64);
     ctx_free(c, c->params32);
     ctx_free(c, c->norms);
     c->params64 = ctx_alloc(c, pbytes);
     c->params32 = ctx_alloc(c, sizeof(float) * p);
     c->norms = ctx_alloc(c, sizeof(float) * (2 * kMaxL + 3 * (size_t)n));
-    if (!c->params64 || !c->params32 || !c->norms) throw PcError(PC_ERR_OOM, "parameter allocation failed");
+    if (!c->params64 || !c->params32 || !c->norms) {
+      ctx_free(c, c->params64);
+      ctx_free(c, c->params32);
+      ctx_free(c, c->norms);
+      throw PcError(PC_ERR_OOM, "parameter allocation failed");
+    }
     c->params_cap = p;
     c->norms_cap = n;
   }
@@ -576,7 +616,7 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   const size_t zs = zsize_of(net.precision);
   const bool reshape = !c->bufs.X || c->shape_D != D || c->shape_S < net.S || c->shape_H < hmax ||
                        c->shape_zs != zs || c->shape_tape != c->opt.keep_tape ||
-                       (c->opt.keep_tape && c->bufs.nz < L);
+                       (c->opt.keep_tape && c->shape_nz < L);
   if (reshape) {
     long long V = std::max<long long>(c->Vcap, std::max<long long>(c->opt.init_vcap, 1 << 14));
     long long E = std::max<long long>(c->Ecap, std::max<long long>(c->opt.init_ecap, (long long)D * V));
@@ -587,6 +627,7 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     c->shape_H = hmax;
     c->shape_zs = zs;
     c->shape_tape = c->opt.keep_tape;
+    c->shape_nz = L;
     realloc_state(c, V, E, T, false);
   } else {
     PC_CUDA(cudaMemsetAsync(c->bufs.table, 0xff, sizeof(uint64_t) * c->Tcap, c->stream));
@@ -613,6 +654,7 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     PC_CUDA(cudaStreamSynchronize(c->stream));
     Global g = *static_cast<Global*>(c->h_g);
     if (g.error & kErrTimeout) throw PcError(PC_ERR_TIMEOUT, "a device-side grid barrier timed out");
+    if (g.error & kErrCorrupt) throw PcError(PC_ERR_CUDA, "a device counter left its capacity (internal error)");
     if (g.halted_at < 0) break;
     if (attempt > 60) throw PcError(PC_ERR_OOM, "capacity growth did not converge");
     // grow what ran out and resume at the halted neuron
@@ -644,10 +686,9 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     double diam = 0.0;
     for (int d = 0; d < D; ++d) diam += (hi[d] - lo[d]) * (hi[d] - lo[d]);
     const float thr = static_cast<float>((c->opt.polish_tol > 0 ? c->opt.polish_tol : 1e-6) * std::sqrt(diam));
-    const size_t psmem = c->res_smem * kWarps;
-    PC_CUDA(cudaFuncSetAttribute(k_polish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
+    const int wpc = std::max(1, std::min(kWarps, int(kPolishSmemMax / c->res_smem)));
     TimerScope ts(c, pc_ctx::kPolishSlot);
-    k_polish<<<c->grid_step, kBlock, psmem, c->stream>>>(net, make_state(c), thr, c->mw);
+    k_polish<<<c->grid_step, 32 * wpc, c->res_smem * wpc, c->stream>>>(net, make_state(c), thr, c->mw);
     PC_CUDA(cudaGetLastError());
     c->launches += 1;
     PC_CUDA(cudaMemcpyAsync(c->h_g, c->g, sizeof(Global), cudaMemcpyDeviceToHost, c->stream));
@@ -699,6 +740,40 @@ void StateBufs::release(pc_ctx* c) {
   ctx_free(c, tape_t);
 }
 
+// Dynamic shared-memory limits of the kernels, set to constant maxima so that
+// every context (in any thread) agrees; a per-network value would race.
+void pc_adjoint_set_attributes();
+static cudaError_t set_func_attributes_now() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f, int bytes) {
+    const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = r;
+  };
+  set((const void*)k_layer<double, false>, kNewtonSmemMax);
+  set((const void*)k_layer<float, false>, kNewtonSmemMax);
+  set((const void*)k_layer<float, true>, kNewtonSmemMax);
+  set((const void*)k_classify<double, false>, kNewtonSmemMax);
+  set((const void*)k_classify<float, false>, kNewtonSmemMax);
+  set((const void*)k_classify<float, true>, kNewtonSmemMax);
+  set((const void*)k_polish, kPolishSmemMax);
+  pc_adjoint_set_attributes();
+  return e;
+}
+
+// Once per device and process, before any launch of these kernels: setting an
+// attribute while another thread launches the kernel is not safe.
+static cudaError_t set_func_attributes() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return cudaSuccess;
+  const cudaError_t e = set_func_attributes_now();
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 
@@ -732,6 +807,11 @@ pc_status pc_create(pc_ctx** out, int device, const pc_options* opt) {
   }
   cudaSetDevice(device);
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (set_func_attributes() != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return PC_ERR_CUDA;
+  }
   *out = c;
   return PC_OK;
 }
@@ -964,6 +1044,10 @@ extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const doub
     g_noalloc_addr[dev] = addr;
   }
   unsigned char* base = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  if (set_func_attributes() != cudaSuccess) {
+    cudaGetLastError();
+    return PC_ERR_CUDA;
+  }
   pc_ctx c;  // host-side descriptor only: its buffers point into the scratch and the caller's arrays
   c.device = dev;
   cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1040,9 +1124,8 @@ extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const doub
       double diam = 0.0;
       for (int d = 0; d < D; ++d) diam += (hi[d] - lo[d]) * (hi[d] - lo[d]);
       const float thr = static_cast<float>(c.opt.polish_tol * std::sqrt(diam));
-      const size_t psmem = c.res_smem * kWarps;
-      PC_CUDA(cudaFuncSetAttribute(k_polish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
-      k_polish<<<c.grid_step, kBlock, psmem, c.stream>>>(net, make_state(&c), thr, c.mw);
+      const int wpc = std::max(1, std::min(kWarps, int(kPolishSmemMax / c.res_smem)));
+      k_polish<<<c.grid_step, 32 * wpc, c.res_smem * wpc, c.stream>>>(net, make_state(&c), thr, c.mw);
       PC_CUDA(cudaGetLastError());
     }
     Global g{};
@@ -1051,6 +1134,7 @@ extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const doub
     PC_CUDA(cudaMemcpyAsync(hc.data(), c.cnt, sizeof(Counters) * (nn + 1), cudaMemcpyDeviceToHost, c.stream));
     PC_CUDA(cudaStreamSynchronize(c.stream));
     if (g.error & kErrTimeout) return PC_ERR_TIMEOUT;
+    if (g.error & kErrCorrupt) return PC_ERR_CUDA;
     if (g.halted_at >= 0) return PC_ERR_OOM;
     bool pairing = (g.error & (kErrPairing | kErrProbe | kErrConflict)) != 0;
     for (int k = 1; k <= nn; ++k)

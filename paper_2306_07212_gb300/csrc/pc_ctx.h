@@ -61,7 +61,9 @@ struct pc_ctx {
   // state
   StateBufs bufs;
   long long Vcap = 0, Ecap = 0, Tcap = 0;
-  int shape_D = 0, shape_S = 0, shape_H = 0, shape_tape = -1;
+  // shape the state buffers were sized for (rows per array); every network
+  // that runs without reshaping fits it
+  int shape_D = 0, shape_S = 0, shape_H = 0, shape_tape = -1, shape_nz = 0;
   size_t shape_zs = 0;
   void* cnt = nullptr;
   int cnt_slots = 0;

@@ -46,6 +46,8 @@ constexpr int kErrDegenerate = 2;
 constexpr int kErrTimeout = 4;
 constexpr int kErrProbe = 8;
 constexpr int kErrConflict = 16;
+constexpr int kErrCorrupt = 32;   // a counter outside its capacity: stop, never index with it
+constexpr int kErrFatal = kErrTimeout | kErrCorrupt;
 
 // halt reasons
 constexpr int kHaltV = 1, kHaltE = 2, kHaltT = 4, kHaltTape = 8;

@@ -16,9 +16,14 @@
 
 namespace pc {
 
-__host__ __device__ inline int newton_ws_doubles(int mw, int D) {
+__host__ __device__ constexpr int newton_ws_doubles(int mw, int D) {
   return 2 * mw + mw * D + D * D + 3 * D + 8 + kMaxWords;  // J, Jn are float
 }
+
+// Upper bounds of the dynamic shared memory of the kernels that use the
+// Newton workspace; the launch attributes are set once to these constants.
+constexpr int kNewtonSmemMax = newton_ws_doubles(kMaxWidth, kMaxD) * 8;
+constexpr int kPolishSmemMax = 160 * 1024;
 
 struct NewtonOut {
   double z;             // value of the target neuron at the exact vertex

@@ -198,6 +198,10 @@ __device__ void phase_classify(const NetDesc& net, const State& st, int zb, int 
   const long long nV = prev->nV_before + prev->nsplit;
   const long long nE = prev->nE_before + prev->nsplit + prev->npairs;
   Counters* cur = st.cnt + n + 1;
+  if (nV < 0 || nV > st.Vcap || nE < 0 || nE > st.Ecap) {
+    if (threadIdx.x == 0) atomicOr(&st.g->error, kErrCorrupt);
+    return;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     cur->nV_before = nV;
     cur->nE_before = nE;
@@ -357,6 +361,10 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
   __syncthreads();
   block_scan_pref(sm, G);
   const long long total = sm.pref[G];
+  if (total < 0 || total > nE || nV < 0 || nV > st.Vcap || nE > st.Ecap) {
+    if (threadIdx.x == 0) atomicOr(&st.g->error, kErrCorrupt);
+    return true;
+  }
   const int D = net.D, m = net.m, S = net.S;
   const int R = D > 1 ? 2 * (D - 1) : 1;
   const long long kmax = total * (long long)(D - 1) * 2;

@@ -127,3 +127,17 @@ def test_zero_residual_and_degree_any_size(cuda):
     # nothing: the recorded sign was decided at the exact vertex)
     sure = (S != 0) & (np.abs(vals) > 1e-5)
     assert np.all(np.sign(vals[sure]) == S[sure])
+
+
+def test_context_keeps_its_buffer_shape_through_growth(cuda):
+    """A context that grew its buffers while running a narrow network must
+    still fit a wider network that it had sized for before."""
+    wide = wl.he_normal_mlp([2, 96, 96, 1], seed=31)
+    narrow = wl.he_normal_mlp([2, 8, 8, 8, 1], seed=32)
+    box = wl.Box.cube(2)
+    with cuda(precision="mixed", init_vcap=64, init_ecap=64) as ex:
+        for net in (wide, narrow, wide):
+            ref = oracle.extract(net, box)
+            ex.extract(net, box)
+            assert_same_complex(_gpu_triple(ex), (ref.X, ref.S, ref.E), coord_tol=_tol(box),
+                                what=f"sequence {net.widths}")
