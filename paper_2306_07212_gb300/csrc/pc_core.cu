@@ -110,11 +110,11 @@ template <typename ZT, bool MIXED>
 __global__ void __launch_bounds__(128) k_gemm_simt(NetDesc net, State st, int l) {
   constexpr int TJ = 16;
   constexpr bool TRACK = sizeof(ZT) == 4;
-  if (st.g->halted_at >= 0 || (st.g->error & kErrFatal)) return;
+  if (cta_stopped(st)) return;
   const Counters* c = st.cnt + net.off[l];
   const long long nV = c->nV_before + c->nsplit;
   if (nV < 0 || nV > st.Vcap) {
-    if (threadIdx.x == 0) atomicOr(&st.g->error, kErrCorrupt);
+    if (threadIdx.x == 0) report_corrupt(st.g, 1, l, nV, st.Vcap, 0);
     return;
   }
   const int H = net.w[l + 1], K = net.w[l];
@@ -194,30 +194,27 @@ __global__ void __launch_bounds__(128) k_gemm_simt(NetDesc net, State st, int l)
 // ---------------------------------------------------------------------------
 // Neuron phases: stepwise kernels and the persistent per-layer kernel.
 
-__device__ __forceinline__ bool stopped(const State& st) {
-  return st.g->halted_at >= 0 || (*(volatile int*)&st.g->error & kErrFatal);
-}
 
 template <typename ZT, bool MIXED>
 __global__ void __launch_bounds__(kBlock, 2) k_classify(NetDesc net, State st, int l, int i, int mw) {
   extern __shared__ double dsm[];
   __shared__ Smem sm;
-  if (stopped(st)) return;
+  if (cta_stopped(st)) return;
   phase_classify<ZT, MIXED>(net, st, l, l, i, net.off[l] + i, sm, dsm, mw);
 }
 
 __global__ void __launch_bounds__(kBlock) k_reclassify(NetDesc net, State st, int l, int i) {
   __shared__ Smem sm;
-  if (stopped(st)) return;
+  if (cta_stopped(st)) return;
   const int n = net.off[l] + i;
-  if (*(volatile int*)&st.g->flip_at != n) return;
+  if (*(volatile int*)&st.g->flip_at != n) return;  // written by the previous launch only
   phase_reclassify(net, st, n, sm);
 }
 
 template <typename ZT, bool MIXED>
 __global__ void __launch_bounds__(kBlock, 2) k_split(NetDesc net, State st, int l, int i) {
   __shared__ Smem sm;
-  if (stopped(st)) return;
+  if (cta_stopped(st)) return;
   phase_split<ZT, MIXED>(net, st, l, l, i, net.off[l] + i, sm);
 }
 
@@ -225,19 +222,21 @@ template <typename ZT, bool MIXED>
 __global__ void __launch_bounds__(kBlock, 2) k_layer(NetDesc net, State st, int l, int i_begin, int mw) {
   extern __shared__ double dsm[];
   __shared__ Smem sm;
-  if (stopped(st)) return;
+  if (cta_stopped(st)) return;
   unsigned int passed = 0;
   const int H = net.w[l + 1];
   for (int i = i_begin; i < H; ++i) {
     const int n = net.off[l] + i;
     phase_classify<ZT, MIXED>(net, st, l, l, i, n, sm, dsm, mw);
-    if (!grid_barrier(st.g, passed) || stopped(st)) return;
+    if (!grid_barrier(st.g, passed)) return;  // uniform per CTA
+    if (cta_stopped(st)) return;
     if (MIXED && *(volatile int*)&st.g->flip_at == n) {
       phase_reclassify(net, st, n, sm);
       if (!grid_barrier(st.g, passed)) return;
     }
     if (phase_split<ZT, MIXED>(net, st, l, l, i, n, sm)) return;
-    if (!grid_barrier(st.g, passed) || stopped(st)) return;
+    if (!grid_barrier(st.g, passed)) return;
+    if (cta_stopped(st)) return;
   }
 }
 
@@ -250,7 +249,7 @@ __global__ void __launch_bounds__(kBlock) k_polish(NetDesc net, State st, float 
   extern __shared__ double dsm[];
   __shared__ int zl[kWarps][kMaxD + 2];
   __shared__ NewtonOut nout[kWarps];
-  if (stopped(st)) return;
+  if (cta_stopped(st)) return;
   const Counters* last = st.cnt + net.N;
   const long long nV = last->nV_before + last->nsplit;
   const long long Vcap = st.Vcap;
@@ -329,6 +328,10 @@ static size_t zsize_of(int prec) { return prec == PC_PREC_FP64 ? 8 : 4; }
 // are (re)shaped), which covers every network that runs without reshaping,
 // not from the current network (a later, wider one would overrun them).
 static void realloc_state(pc_ctx* c, long long V, long long E, long long T, bool copy) {
+  // multiples of 64 entries: rows stay 256-byte aligned (vector loads of the
+  // second endpoint row need EW = EU + Ecap on a 16-byte boundary)
+  V = std::min<long long>((V + 63) & ~63ll, (1ll << 31) - 64);
+  E = std::min<long long>((E + 63) & ~63ll, (1ll << 31) - 64);
   const int D = c->shape_D, S = c->shape_S, Hm = c->shape_H;
   const size_t zs = c->shape_zs;
   StateBufs nb;
@@ -399,13 +402,13 @@ static void ensure_fixed(pc_ctx* c, int N) {
     ctx_free(c, c->g);
     ctx_free(c, c->cta);
     c->g = ctx_alloc(c, sizeof(Global));
-    c->cta = ctx_alloc(c, sizeof(long long) * kMaxGrid);
+    c->cta = ctx_alloc(c, sizeof(long long) * 2 * kMaxGrid);  // counts, then their step tags
     if (!c->g || !c->cta) {
       ctx_free(c, c->g);
       ctx_free(c, c->cta);
       throw PcError(PC_ERR_OOM, "status allocation failed");
     }
-    PC_CUDA(cudaMemsetAsync(c->cta, 0, sizeof(long long) * kMaxGrid, c->stream));
+    PC_CUDA(cudaMemsetAsync(c->cta, 0, sizeof(long long) * 2 * kMaxGrid, c->stream));
     if (!c->h_g && cudaMallocHost(&c->h_g, sizeof(Global)) != cudaSuccess) {
       cudaGetLastError();
       c->h_g = nullptr;
@@ -654,7 +657,11 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     PC_CUDA(cudaStreamSynchronize(c->stream));
     Global g = *static_cast<Global*>(c->h_g);
     if (g.error & kErrTimeout) throw PcError(PC_ERR_TIMEOUT, "a device-side grid barrier timed out");
-    if (g.error & kErrCorrupt) throw PcError(PC_ERR_CUDA, "a device counter left its capacity (internal error)");
+    if (g.error & kErrCorrupt)
+      throw PcError(PC_ERR_CUDA, "a device counter left its capacity (internal error; check " +
+                                     std::to_string(g.diag_site) + " at " + std::to_string(g.diag_n) + ": " +
+                                     std::to_string(g.diag_a) + " " + std::to_string(g.diag_b) + " " +
+                                     std::to_string(g.diag_c) + ")");
     if (g.halted_at < 0) break;
     if (attempt > 60) throw PcError(PC_ERR_OOM, "capacity growth did not converge");
     // grow what ran out and resume at the halted neuron
@@ -673,6 +680,7 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     PC_CUDA(cudaMemsetAsync(&static_cast<Counters*>(c->cnt)[hn].tsize, 0, sizeof(long long), c->stream));
     Global g0{};
     g0.halted_at = -1;
+    g0.flip_at = -1;
     g0.error = g.error;
     *static_cast<Global*>(c->h_g) = g0;
     PC_CUDA(cudaMemcpyAsync(c->g, c->h_g, sizeof(Global), cudaMemcpyHostToDevice, c->stream));
@@ -712,14 +720,23 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   const Global g = *static_cast<Global*>(c->h_g);
   long long degenerate = 0, undecided = 0;
   bool pairing = (g.error & (kErrPairing | kErrProbe)) != 0;
+  int pair_at = -1;
   for (int k = 1; k <= n; ++k) {
     degenerate += hc[k].ndegenerate;
     undecided += hc[k].nundecided;
-    if (hc[k].nkeys != 2 * hc[k].npairs) pairing = true;
+    if (hc[k].nkeys != 2 * hc[k].npairs && pair_at < 0) pair_at = k - 1;
   }
+  pairing = pairing || pair_at >= 0;
   c->degenerate = degenerate;
   c->undecided = undecided;
-  if (pairing) throw PcError(PC_ERR_PAIRING, "a splitting 2-face did not occur exactly twice (non-generic input)");
+  if (pairing) {
+    std::string where = pair_at >= 0 ? " at neuron " + std::to_string(pair_at) + ": " +
+                                           std::to_string(hc[pair_at + 1].nkeys) + " keys, " +
+                                           std::to_string(hc[pair_at + 1].npairs) + " pairs"
+                                     : "";
+    throw PcError(PC_ERR_PAIRING, "a splitting 2-face did not occur exactly twice (non-generic input; error bits " +
+                                      std::to_string(g.error) + where + ")");
+  }
   if (g.error & kErrConflict) throw PcError(PC_ERR_PAIRING, "edge endpoints disagree on a processed sign entry");
   if (c->opt.strict && (degenerate || undecided))
     throw PcError(PC_ERR_DEGENERATE, "genericity violated: " + std::to_string(degenerate) + " exact zeros, " +
@@ -997,7 +1014,7 @@ constexpr size_t kNaOffTable = kNaOffStage + na_align(16 * kNaMaxE);
 constexpr size_t kNaOffCnt = kNaOffTable + na_align(8 * kNaMaxT);
 constexpr size_t kNaOffG = kNaOffCnt + na_align(sizeof(Counters) * (kNaMaxN + 1));
 constexpr size_t kNaOffCta = kNaOffG + na_align(sizeof(Global));
-constexpr size_t kNaBytes = kNaOffCta + na_align(8 * kMaxGrid);
+constexpr size_t kNaBytes = kNaOffCta + na_align(8 * 2 * kMaxGrid);
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 

@@ -84,8 +84,21 @@ struct Global {
   unsigned int pad1;
   long long need_v, need_e, need_t;
   long long polished;
-  long long pad[2];
+  int diag_site;         // first failed consistency check (1 forward product, 2 classify, 3 split), 0: none
+  int diag_n;            // its neuron (layer for the forward product)
+  long long diag_a, diag_b, diag_c;  // the values it found
 };
+
+// Flags kErrCorrupt and records the first failing check with its values.
+__device__ __forceinline__ void report_corrupt(Global* g, int site, int n, long long a, long long b, long long c) {
+  if (atomicCAS(&g->diag_site, 0, site) == 0) {
+    g->diag_n = n;
+    g->diag_a = a;
+    g->diag_b = b;
+    g->diag_c = c;
+  }
+  atomicOr(&g->error, kErrCorrupt);
+}
 
 struct State {
   long long Vcap, Ecap, Tcap;
@@ -144,6 +157,18 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
   unsigned int v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+__device__ __forceinline__ bool stopped(const State& st) {
+  return *(volatile int*)&st.g->halted_at >= 0 || (*(volatile int*)&st.g->error & kErrFatal);
+}
+
+// The stop flags read once per CTA and shared by all its threads.  Another
+// CTA of the same launch may raise a flag (a capacity halt, an error) while
+// this CTA's warps start; a per-thread read would then let part of the CTA
+// return and leave the rest waiting at barriers with partial block data.
+__device__ __forceinline__ bool cta_stopped(const State& st) {
+  return __syncthreads_or(threadIdx.x == 0 && stopped(st)) != 0;
 }
 
 // Grid-wide barrier for cooperative launches.  Bounded: after ~0.5 s of

@@ -114,6 +114,9 @@ __device__ __forceinline__ int block_offsets(Smem& sm, int c) {
   return int(sm.wsum[warp]) + x - c;
 }
 
+// Tag stored beside each CTA's count: identifies the step that wrote it.
+__device__ __forceinline__ long long cta_tag(int n, long long nE) { return nE * 65536 + n + 1; }
+
 // Edge range of this CTA in the compaction (a multiple of 4 edges per CTA).
 __device__ __forceinline__ void cta_range(long long nE, long long& chunk, long long& begin, long long& end) {
   const long long G = gridDim.x;
@@ -128,7 +131,7 @@ __device__ __forceinline__ void cta_range(long long nE, long long& chunk, long l
 // (after every sign is final); otherwise from the sign of the stored value.
 template <typename ZT, bool FROM_CODES>
 __device__ long long compact_edges(const State& st, const ZT* zrow, int e, long long begin, long long end,
-                                   Smem& sm) {
+                                   long long nV, int n, Smem& sm) {
   const int sh = 2 * (e & 31);
   const uint64_t* sw = st.SIG + (long long)(e >> 5) * st.Vcap;
   long long count = 0;
@@ -158,7 +161,9 @@ __device__ long long compact_edges(const State& st, const ZT* zrow, int e, long 
     for (int q = 0; q < 4; ++q) {
       split[q] = false;
       uplus[q] = true;
-      if (q < nvalid) {
+      if (q < nvalid && (pu[q] < 0 || pu[q] >= nV || pw[q] < 0 || pw[q] >= nV)) {
+        report_corrupt(st.g, 6, n, idx0 + q, pu[q], pw[q]);  // never index with it
+      } else if (q < nvalid) {
         bool su, sv;
         if (FROM_CODES) {
           su = ((sw[pu[q]] >> sh) & 3ull) == kMinus;
@@ -199,7 +204,7 @@ __device__ void phase_classify(const NetDesc& net, const State& st, int zb, int 
   const long long nE = prev->nE_before + prev->nsplit + prev->npairs;
   Counters* cur = st.cnt + n + 1;
   if (nV < 0 || nV > st.Vcap || nE < 0 || nE > st.Ecap) {
-    if (threadIdx.x == 0) atomicOr(&st.g->error, kErrCorrupt);
+    if (threadIdx.x == 0) report_corrupt(st.g, 2, n, nV, nE, st.Vcap);
     return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -281,8 +286,11 @@ __device__ void phase_classify(const NetDesc& net, const State& st, int zb, int 
   // step (3): splitting edges, speculatively from the signs of the values
   long long chunk, begin, end;
   cta_range(nE, chunk, begin, end);
-  const long long count = compact_edges<ZT, false>(st, zrow, e, begin, end, sm);
-  if (threadIdx.x == 0) st.cta_count[blockIdx.x] = count;
+  const long long count = compact_edges<ZT, false>(st, zrow, e, begin, end, nV, n, sm);
+  if (threadIdx.x == 0) {
+    st.cta_count[blockIdx.x] = count;
+    st.cta_count[kMaxGrid + blockIdx.x] = cta_tag(n, nE);
+  }
   ndeg = warp_sum_ll(ndeg);
   if (lane == 0 && ndeg) atomic_add_ll(&cur->ndegenerate, ndeg);
   if (MIXED && threadIdx.x == 0 && und) atomic_add_ll(&cur->nundecided, (long long)und);
@@ -291,11 +299,14 @@ __device__ void phase_classify(const NetDesc& net, const State& st, int zb, int 
 // Step (3) again from the final sign codes, for a step whose FP64 re-decision
 // flipped a sign that the speculative pass had used.
 __device__ __forceinline__ void phase_reclassify(const NetDesc& net, const State& st, int n, Smem& sm) {
-  const long long nE = st.cnt[n + 1].nE_before;
+  const long long nV = st.cnt[n + 1].nV_before, nE = st.cnt[n + 1].nE_before;
   long long chunk, begin, end;
   cta_range(nE, chunk, begin, end);
-  const long long count = compact_edges<float, true>(st, nullptr, net.m + n, begin, end, sm);
-  if (threadIdx.x == 0) st.cta_count[blockIdx.x] = count;
+  const long long count = compact_edges<float, true>(st, nullptr, net.m + n, begin, end, nV, n, sm);
+  if (threadIdx.x == 0) {
+    st.cta_count[blockIdx.x] = count;
+    st.cta_count[kMaxGrid + blockIdx.x] = cta_tag(n, nE);
+  }
 }
 
 // Whole-warp check that the 2-face key of split edge k2 (payload r2 =
@@ -305,14 +316,22 @@ __device__ __forceinline__ void phase_reclassify(const NetDesc& net, const State
 // does not modify, so no memory fence is needed.  All lanes must call it.
 __device__ __forceinline__ bool warp_face_matches(const State& st, const Smem& sm, int G, long long chunk,
                                                   long long k2, int r2, int e, int S, uint64_t s0,
-                                                  int wj, uint64_t Fw) {
+                                                  int wj, uint64_t Fw, long long nV, long long total, int n) {
   const int lane = threadIdx.x & 31;
+  if (k2 < 0 || k2 >= total) {  // a payload that no split of this step wrote
+    if (lane == 0) report_corrupt(st.g, 5, n, k2, total, r2);
+    return false;
+  }
   int lo = 0, hi = G - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (sm.pref[mid] <= k2) lo = mid; else hi = mid - 1;
   }
   const int4 s2 = st.stage[lo * chunk + (k2 - sm.pref[lo])];
+  if (s2.y < 0 || s2.y >= nV || s2.z < 0 || s2.z >= nV) {
+    if (lane == 0) report_corrupt(st.g, 7, n, k2, s2.y, s2.z);
+    return false;
+  }
   const long long Vcap = st.Vcap;
   const int wn = e >> 5, sh = 2 * (e & 31);
   uint64_t w2 = 0, zm = 0;
@@ -353,7 +372,21 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
   Counters* cur = st.cnt + n + 1;
   const long long nV = cur->nV_before, nE = cur->nE_before;
   const int G = gridDim.x;
-  for (int q = threadIdx.x; q < G; q += kBlock) sm.pref[q] = st.cta_count[q];
+  {
+    // every CTA range of this step must carry a count written for this step
+    long long chunk0, b0_, b1_;
+    cta_range(nE, chunk0, b0_, b1_);
+    int bad = 0;
+    for (int q = threadIdx.x; q < G; q += kBlock) {
+      const long long cq = st.cta_count[q], tq = st.cta_count[kMaxGrid + q];
+      sm.pref[q] = cq;
+      if (tq != cta_tag(n, nE) || cq < 0 || cq > chunk0) {
+        report_corrupt(st.g, 8, n, q, tq, cq);
+        bad = 1;
+      }
+    }
+    if (__syncthreads_or(bad)) return true;
+  }
   if (threadIdx.x == 0) {
     sm.npairs = 0;
     sm.acc[0] = sm.acc[1] = 0;
@@ -362,7 +395,7 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
   block_scan_pref(sm, G);
   const long long total = sm.pref[G];
   if (total < 0 || total > nE || nV < 0 || nV > st.Vcap || nE > st.Ecap) {
-    if (threadIdx.x == 0) atomicOr(&st.g->error, kErrCorrupt);
+    if (threadIdx.x == 0) report_corrupt(st.g, 3, n, total, nV, nE);
     return true;
   }
   const int D = net.D, m = net.m, S = net.S;
@@ -411,6 +444,10 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
     }
     const int4 sg = st.stage[lo * chunk + (k - sm.pref[lo])];
     const int32_t ed = sg.x, p = sg.y, q = sg.z;  // p: V+, q: V-
+    if (ed < 0 || ed >= nE || p < 0 || p >= nV || q < 0 || q >= nV) {  // warp-uniform
+      if (lane == 0) report_corrupt(st.g, 4, n, ed, p, q);
+      continue;
+    }
     const double a = static_cast<double>(Z[(long long)i * Vcap + p]);
     const double b = static_cast<double>(Z[(long long)i * Vcap + q]);
     double xp = 0.0, xq = 0.0;
@@ -565,7 +602,8 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
         const uint64_t pp = __shfl_sync(0xffffffffu, old, L) & 0x7fffffffull;
         const int wjL = __shfl_sync(0xffffffffu, wj, L);
         const uint64_t FwL = __shfl_sync(0xffffffffu, Fw, L);
-        const bool eq = warp_face_matches(st, sm, G, chunk, (long long)(pp / R), int(pp % R), e, S, s0, wjL, FwL);
+        const bool eq = warp_face_matches(st, sm, G, chunk, (long long)(pp / R), int(pp % R), e, S, s0, wjL, FwL,
+                                          nV, total, n);
         if (lane == L) {
           if (eq) {
             const uint64_t prev = atomicOr(reinterpret_cast<unsigned long long*>(st.table + slot),
