@@ -69,6 +69,13 @@ typedef enum {
   PC_EXEC_STEPWISE = 1    /* one kernel per step and neuron */
 } pc_exec;
 
+typedef enum {
+  PC_GEMM_TENSOR = 0,  /* tcgen05 3xTF32 tensor-core product for layers with
+                          widths <= 128 (FP32 and mixed precision), SIMT FP32
+                          otherwise; the first layer (K = D) is always FP64 FMA */
+  PC_GEMM_SIMT = 1     /* SIMT FP32 FMA for every layer */
+} pc_gemm;
+
 typedef struct {
   int precision;          /* pc_precision */
   int exec;               /* pc_exec */
@@ -85,10 +92,12 @@ typedef struct {
                              PC_PREC_MIXED only */
   double polish_tol;      /* relative to the box diameter (default 1e-6) */
   int timers;             /* record CUDA events around each layer's kernels */
+  int gemm;               /* pc_gemm: layer-start product of FP32 values */
 } pc_options;
 
 /* Fills *opt with defaults (mixed precision, persistent execution,
- * filter_kappa 12, polish in mixed precision with polish_tol 1e-6). */
+ * filter_kappa 12, polish in mixed precision with polish_tol 1e-6, tensor-core
+ * layer products). */
 void pc_default_options(pc_options *opt);
 
 /* Creates a context on CUDA device `device`.  opt may be NULL (defaults). */

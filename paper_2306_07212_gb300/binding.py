@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "PC_OK", 1: "PC_ERR_INVALID", 2: "PC_ERR_OOM", 3: "PC_ERR_CUD
                 4: "PC_ERR_DEGENERATE", 5: "PC_ERR_PAIRING", 6: "PC_ERR_TOO_LARGE",
                 7: "PC_ERR_TIMEOUT", 8: "PC_ERR_NO_TAPE", 9: "PC_PENDING"}
 PRECISION = {"fp32": 0, "mixed": 1, "fp64": 2}
+GEMM = {"tensor": 0, "simt": 1}
 EXEC = {"persistent": 0, "stepwise": 1}
 
 # Every symbol include/pc.h declares (checked by the tests).
@@ -54,7 +55,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("exec", ctypes.c_int), ("keep_tape", ctypes.c_int),
                 ("strict", ctypes.c_int), ("init_vcap", ctypes.c_int64), ("init_ecap", ctypes.c_int64),
                 ("mem_budget_bytes", ctypes.c_int64), ("filter_kappa", ctypes.c_double),
-                ("polish", ctypes.c_int), ("polish_tol", ctypes.c_double), ("timers", ctypes.c_int)]
+                ("polish", ctypes.c_int), ("polish_tol", ctypes.c_double), ("timers", ctypes.c_int),
+                ("gemm", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -146,7 +148,7 @@ class Extractor:
     def __init__(self, device: int = 0, precision: str = "mixed", execution: str = "persistent",
                  keep_tape: bool = False, strict: bool = False, init_vcap: int = 0, init_ecap: int = 0,
                  mem_budget_bytes: int = 0, kappa: float = 12.0, polish: int = -1, polish_tol: float = 1e-6,
-                 timers: bool = False, torch_allocator: bool = True):
+                 timers: bool = False, torch_allocator: bool = True, gemm: str = "tensor"):
         self._lib = load_library()
         o = Options()
         self._lib.pc_default_options(ctypes.byref(o))
@@ -160,6 +162,7 @@ class Extractor:
         o.polish = int(polish)
         o.polish_tol = float(polish_tol)
         o.timers = int(timers)
+        o.gemm = GEMM[gemm]
         self.device = device
         self.options = o
         self._ctx = ctypes.c_void_p()

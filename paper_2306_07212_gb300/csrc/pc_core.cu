@@ -471,6 +471,11 @@ template <typename ZT, bool MIXED>
 struct Kernels {
   static void gemm(pc_ctx* c, const State& st, int l) {
     TimerScope ts(c, 2 * l);
+    if (sizeof(ZT) == 4 && c->opt.gemm == PC_GEMM_TENSOR && pc_gemm_tc_eligible(c->net, l)) {
+      PC_CUDA(pc_gemm_tc_launch(c->net, st, l, (c->Vcap + 127) / 128, c->num_sms, c->stream));
+      c->launches += 1;
+      return;
+    }
     const int H = c->net.w[l + 1];
     dim3 grid(std::max(1, std::min<int>(c->num_sms * 8, int((c->Vcap + 127) / 128))), (H + 15) / 16);
     k_gemm_simt<ZT, MIXED><<<grid, 128, 0, c->stream>>>(c->net, st, l);
@@ -773,6 +778,10 @@ static cudaError_t set_func_attributes_now() {
   set((const void*)k_classify<float, false>, kNewtonSmemMax);
   set((const void*)k_classify<float, true>, kNewtonSmemMax);
   set((const void*)k_polish, kPolishSmemMax);
+  {
+    const cudaError_t r = pc_gemm_tc_set_attributes();
+    if (e == cudaSuccess) e = r;
+  }
   pc_adjoint_set_attributes();
   return e;
 }
@@ -818,7 +827,8 @@ pc_status pc_create(pc_ctx** out, int device, const pc_options* opt) {
   c->device = device;
   pc_default_options(&c->opt);
   if (opt) c->opt = *opt;
-  if (c->opt.precision < 0 || c->opt.precision > 2 || c->opt.exec < 0 || c->opt.exec > 1) {
+  if (c->opt.precision < 0 || c->opt.precision > 2 || c->opt.exec < 0 || c->opt.exec > 1 || c->opt.gemm < 0 ||
+      c->opt.gemm > 1) {
     delete c;
     return PC_ERR_INVALID;
   }

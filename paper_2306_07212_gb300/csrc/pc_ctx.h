@@ -17,6 +17,12 @@ void* ctx_alloc(pc_ctx* c, size_t bytes);
 void ctx_free(pc_ctx* c, void*& p);
 pc::State pc_make_state(pc_ctx* c);
 
+// tcgen05 3xTF32 layer-start product (pc_gemm_tc.cu)
+bool pc_gemm_tc_eligible(const pc::NetDesc& net, int l);
+cudaError_t pc_gemm_tc_set_attributes();
+cudaError_t pc_gemm_tc_launch(const pc::NetDesc& net, const pc::State& st, int l, long long vcap_tiles, int num_sms,
+                              cudaStream_t stream);
+
 struct PcError : std::runtime_error {
   pc_status status;
   PcError(pc_status s, const std::string& m) : std::runtime_error(m), status(s) {}

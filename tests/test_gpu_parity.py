@@ -141,3 +141,26 @@ def test_context_keeps_its_buffer_shape_through_growth(cuda):
             ex.extract(net, box)
             assert_same_complex(_gpu_triple(ex), (ref.X, ref.S, ref.E), coord_tol=_tol(box),
                                 what=f"sequence {net.widths}")
+
+
+@pytest.mark.parametrize("widths", [[3, 64, 64, 64, 1], [2, 16, 128, 40, 8, 1], [4, 32, 96, 1]])
+def test_tensor_core_product_matches_simt_and_oracle(cuda, widths):
+    """The tcgen05 3xTF32 layer product (default) and the SIMT FP32 product
+    give the oracle's complex; their final-layer values agree to FP32 accuracy."""
+    net = wl.he_normal_mlp(widths, seed=11)
+    box = wl.Box.cube(widths[0])
+    ref = oracle.extract(net, box)
+    with cuda(precision="mixed", gemm="tensor") as a, cuda(precision="mixed", gemm="simt") as b:
+        a.extract(net, box)
+        b.extract(net, box)
+        for ex, name in ((a, "tensor"), (b, "simt")):
+            assert_same_complex(_gpu_triple(ex), (ref.X, ref.S, ref.E), coord_tol=_tol(box), what=f"{widths} {name}")
+        assert a.diagnostics()["launches"] > 0
+        va, vb = a.values(), b.values()
+        assert va.shape == vb.shape
+        # vertices are numbered in creation order, which follows the
+        # (unordered) edge emission: match them by sign vector
+        ka = {r.tobytes(): k for k, r in enumerate(np.ascontiguousarray(a.sign_words().T))}
+        perm = np.array([ka[r.tobytes()] for r in np.ascontiguousarray(b.sign_words().T)])
+        scale = max(1.0, float(np.max(np.abs(vb))))
+        assert float(np.max(np.abs(va[perm] - vb))) <= 1e-4 * scale

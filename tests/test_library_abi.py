@@ -52,4 +52,4 @@ def test_default_options_without_gpu(lib_path):
     lib = binding.load_library()
     o = binding.Options()
     lib.pc_default_options(ctypes.byref(o))
-    assert o.precision == 1 and o.exec == 0 and o.filter_kappa == 12.0 and o.polish == -1
+    assert o.precision == 1 and o.exec == 0 and o.filter_kappa == 12.0 and o.polish == -1 and o.gemm == 0
