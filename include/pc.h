@@ -76,6 +76,17 @@ typedef enum {
   PC_GEMM_SIMT = 1     /* SIMT FP32 FMA for every layer */
 } pc_gemm;
 
+typedef enum {
+  PC_PAIR_DEFERRED = 0, /* 2-faces keyed by a 64-bit fingerprint of their full
+                           sign vector, paired at the second occurrence in
+                           one 128-bit atomic; every pairing is then checked
+                           exactly from the two new vertices' sign vectors,
+                           and a failed check (a fingerprint collision)
+                           repeats the extraction with PC_PAIR_INLINE */
+  PC_PAIR_INLINE = 1    /* 32-bit tag; the second occurrence compares the
+                           full sign vectors before it pairs */
+} pc_pairing;
+
 typedef struct {
   int precision;          /* pc_precision */
   int exec;               /* pc_exec */
@@ -93,6 +104,8 @@ typedef struct {
   double polish_tol;      /* relative to the box diameter (default 1e-6) */
   int timers;             /* record CUDA events around each layer's kernels */
   int gemm;               /* pc_gemm: layer-start product of FP32 values */
+  int pairing;            /* pc_pairing: how step 5 matches the two
+                             occurrences of a splitting 2-face */
 } pc_options;
 
 /* Fills *opt with defaults (mixed precision, persistent execution,
@@ -169,7 +182,8 @@ pc_status pc_backward(pc_ctx *ctx, const double *grad_x, double *grad_params, vo
 /* Diagnostics of the last extraction, up to n int64 values: kernel launches
  * (cumulative over the context's life), capacity growths, polished vertices,
  * exact-zero pre-activations, FP64-undecidable signs, vertex / edge / hash
- * capacities, device bytes held, CTAs of the persistent kernel. */
+ * capacities, device bytes held, CTAs of the persistent kernel, extractions
+ * repeated with inline pairing after a failed fingerprint check (cumulative). */
 pc_status pc_diagnostics(pc_ctx *ctx, int64_t *out, int n);
 
 /* With opt.timers: device time in ms of the last extraction's kernels,

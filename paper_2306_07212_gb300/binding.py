@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "PC_OK", 1: "PC_ERR_INVALID", 2: "PC_ERR_OOM", 3: "PC_ERR_CUD
                 7: "PC_ERR_TIMEOUT", 8: "PC_ERR_NO_TAPE", 9: "PC_PENDING"}
 PRECISION = {"fp32": 0, "mixed": 1, "fp64": 2}
 GEMM = {"tensor": 0, "simt": 1}
+PAIRING = {"deferred": 0, "inline": 1}
 EXEC = {"persistent": 0, "stepwise": 1}
 
 # Every symbol include/pc.h declares (checked by the tests).
@@ -56,7 +57,7 @@ class Options(ctypes.Structure):
                 ("strict", ctypes.c_int), ("init_vcap", ctypes.c_int64), ("init_ecap", ctypes.c_int64),
                 ("mem_budget_bytes", ctypes.c_int64), ("filter_kappa", ctypes.c_double),
                 ("polish", ctypes.c_int), ("polish_tol", ctypes.c_double), ("timers", ctypes.c_int),
-                ("gemm", ctypes.c_int)]
+                ("gemm", ctypes.c_int), ("pairing", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -148,7 +149,8 @@ class Extractor:
     def __init__(self, device: int = 0, precision: str = "mixed", execution: str = "persistent",
                  keep_tape: bool = False, strict: bool = False, init_vcap: int = 0, init_ecap: int = 0,
                  mem_budget_bytes: int = 0, kappa: float = 12.0, polish: int = -1, polish_tol: float = 1e-6,
-                 timers: bool = False, torch_allocator: bool = True, gemm: str = "tensor"):
+                 timers: bool = False, torch_allocator: bool = True, gemm: str = "tensor",
+                 pairing: str = "deferred"):
         self._lib = load_library()
         o = Options()
         self._lib.pc_default_options(ctypes.byref(o))
@@ -163,6 +165,7 @@ class Extractor:
         o.polish_tol = float(polish_tol)
         o.timers = int(timers)
         o.gemm = GEMM[gemm]
+        o.pairing = PAIRING[pairing]
         self.device = device
         self.options = o
         self._ctx = ctypes.c_void_p()
@@ -261,10 +264,10 @@ class Extractor:
         return out
 
     def diagnostics(self) -> dict:
-        out = np.zeros(10, np.int64)
-        self._check(self._lib.pc_diagnostics(self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 10))
+        out = np.zeros(11, np.int64)
+        self._check(self._lib.pc_diagnostics(self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 11))
         keys = ["launches", "grows", "polished", "degenerate", "undecided", "vcap", "ecap", "tcap",
-                "bytes", "persistent_ctas"]
+                "bytes", "persistent_ctas", "reruns"]
         return dict(zip(keys, (int(x) for x in out)))
 
     def kernel_times_ms(self) -> np.ndarray:

@@ -81,6 +81,7 @@ __global__ void k_init(NetDesc net, State st) {
     const int c = ((r >> d) << (d + 1)) | (r & ((1 << d) - 1));
     st.EU[e] = c;
     st.EW[e] = c | (1 << d);
+    if (st.deferred) st.vlist[e] = make_int4(0, 0, 0, 0);
   }
   if (threadIdx.x == 0) {
     Counters c0{};
@@ -240,6 +241,61 @@ __global__ void __launch_bounds__(kBlock, 2) k_layer(NetDesc net, State st, int 
   }
 }
 
+// Exact check of every pairing made by fingerprint (deferred mode), after
+// the last step: the two new vertices' sign vectors, restricted to the
+// entries before the step's neuron, with the keyed zero set to its sign,
+// must be equal (the 2-face of Section 4.2, step 5).  Sign entries below a
+// step's neuron never change after the step, so the check can run at the
+// end.  One thread per edge; non-pairing edges carry a zero record.
+__device__ __forceinline__ void set_keyed_zero(uint64_t& f, uint64_t zm, int& remaining, bool minus) {
+  if (remaining < 0) return;
+  const int c = __popcll(zm);
+  if (remaining >= c) {
+    remaining -= c;
+    return;
+  }
+  for (int q = 0; q < remaining; ++q) zm &= zm - 1;
+  const int bit = __ffsll((long long)zm) - 1;
+  f = (f & ~(3ull << bit)) | ((minus ? kMinus : kPlus) << bit);
+  remaining = -1;
+}
+
+__global__ void __launch_bounds__(256) k_verify_pairs(NetDesc net, State st) {
+  if (cta_stopped(st)) return;
+  const Counters* last = st.cnt + net.N;
+  const long long nE = last->nE_before + last->nsplit + last->npairs;
+  const long long nV = last->nV_before + last->nsplit;
+  if (nE < 0 || nE > st.Ecap || nV < 0 || nV > st.Vcap) {
+    if (threadIdx.x == 0) report_corrupt(st.g, 9, net.N, nV, nE, 0);
+    return;
+  }
+  const long long Vcap = st.Vcap;
+  const int S = net.S, m = net.m;
+  int bad = 0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += (long long)gridDim.x * blockDim.x) {
+    const int4 r = st.vlist[e];
+    if (r.w == 0) continue;
+    const int n = r.w - 1;
+    if (n < 0 || n >= net.N || r.x < 0 || r.x >= nV || r.y < 0 || r.y >= nV) {
+      bad = 1;
+      continue;
+    }
+    const int ent = m + n, ka = r.z >> 16, kb = r.z & 0xffff;
+    int oa = ka >> 1, ob = kb >> 1;
+    bool same = true;
+    for (int w = 0; w < S && 32 * w < ent; ++w) {
+      uint64_t fa = st.SIG[(long long)w * Vcap + r.x], fb = st.SIG[(long long)w * Vcap + r.y];
+      set_keyed_zero(fa, zero_mask(fa, w, ent), oa, ka & 1);
+      set_keyed_zero(fb, zero_mask(fb, w, ent), ob, kb & 1);
+      const int cnt = ent - 32 * w;
+      const uint64_t valid = cnt >= 32 ? ~0ull : ((1ull << (2 * cnt)) - 1);
+      if ((fa ^ fb) & valid) same = false;
+    }
+    if (!same || oa >= 0 || ob >= 0) bad = 1;  // a keyed zero that does not exist also fails
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st.g->error, kErrVerify);
+}
+
 // Coordinate polish: every vertex whose coordinate error estimate (rms)
 // exceeds thr is moved to its exact position by an FP64 Newton step
 // on its D zero entries (all entries are processed at this point).  One warp
@@ -350,12 +406,13 @@ static void realloc_state(pc_ctx* c, long long V, long long E, long long T, bool
   A(nb.SIG, sizeof(uint64_t) * S * V);
   A(nb.E, sizeof(int32_t) * 2 * E);
   A(nb.stage, sizeof(int4) * E);
-  A(nb.table, sizeof(uint64_t) * T);
+  A(nb.vlist, sizeof(int4) * E);
+  A(nb.table, 16 * T);
   if (c->opt.keep_tape) {
     A(nb.tape_pq, sizeof(int32_t) * 2 * V);
     A(nb.tape_t, sizeof(double) * V);
   }
-  PC_CUDA(cudaMemsetAsync(nb.table, 0xff, sizeof(uint64_t) * T, c->stream));
+  PC_CUDA(cudaMemsetAsync(nb.table, 0xff, 16 * T, c->stream));
   StateBufs& ob = c->bufs;
   if (copy && ob.X) {
     const long long oV = c->Vcap, oE = c->Ecap, nV = std::min(oV, V), nE = std::min(oE, E);
@@ -368,6 +425,7 @@ static void realloc_state(pc_ctx* c, long long V, long long E, long long T, bool
     cp2(nb.exc, 4 * V, ob.exc, 4 * oV, 4 * nV, 1);
     cp2(nb.SIG, 8 * V, ob.SIG, 8 * oV, 8 * nV, S);
     cp2(nb.E, 4 * E, ob.E, 4 * oE, 4 * nE, 2);
+    cp2(nb.vlist, 16 * E, ob.vlist, 16 * oE, 16 * nE, 1);
     if (c->opt.keep_tape && ob.tape_pq) {
       cp2(nb.tape_pq, 4 * V, ob.tape_pq, 4 * oV, 4 * nV, 2);
       cp2(nb.tape_t, 8 * V, ob.tape_t, 8 * oV, 8 * nV, 1);
@@ -435,6 +493,8 @@ static State make_state(pc_ctx* c) {
   s.EW = s.EU + c->Ecap;
   s.stage = static_cast<int4*>(c->bufs.stage);
   s.table = static_cast<uint64_t*>(c->bufs.table);
+  s.vlist = static_cast<int4*>(c->bufs.vlist);
+  s.deferred = c->deferred;
   s.cnt = static_cast<Counters*>(c->cnt);
   s.g = static_cast<Global*>(c->g);
   s.cta_count = static_cast<long long*>(c->cta);
@@ -543,6 +603,9 @@ static int occupancy_any(pc_ctx* c) {
   }
 }
 
+// Thrown when the exact check after a fingerprint-paired extraction fails.
+struct NeedsInlinePairing {};
+
 static long long pow2_at_least(long long x) {
   long long p = 64;
   while (p < x) p <<= 1;
@@ -550,7 +613,8 @@ static long long pow2_at_least(long long x) {
 }
 
 static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* params,
-                        const double* lo, const double* hi) {
+                        const double* lo, const double* hi, bool deferred) {
+  c->deferred = deferred ? 1 : 0;
   if (L < 1 || L > kMaxL) throw PcError(PC_ERR_INVALID, "number of layers must be in [1, 16]");
   const int D = widths[0];
   if (D < 1 || D > kMaxD) throw PcError(PC_ERR_INVALID, "input dimension must be in [1, 8]");
@@ -638,7 +702,7 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     c->shape_nz = L;
     realloc_state(c, V, E, T, false);
   } else {
-    PC_CUDA(cudaMemsetAsync(c->bufs.table, 0xff, sizeof(uint64_t) * c->Tcap, c->stream));
+    PC_CUDA(cudaMemsetAsync(c->bufs.table, 0xff, 16 * c->Tcap, c->stream));
   }
   PC_CUDA(cudaMemsetAsync(c->cnt, 0, sizeof(Counters) * (n + 1), c->stream));
 
@@ -694,6 +758,11 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     gemm_done = true;
     c->grows += 1;
   }
+  if (c->deferred) {
+    k_verify_pairs<<<c->grid_step, 256, 0, c->stream>>>(net, make_state(c));
+    PC_CUDA(cudaGetLastError());
+    c->launches += 1;
+  }
   const bool polish = c->opt.polish > 0 || (c->opt.polish < 0 && net.precision == PC_PREC_MIXED);
   if (polish && net.precision != PC_PREC_FP64) {
     double diam = 0.0;
@@ -704,8 +773,8 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     k_polish<<<c->grid_step, 32 * wpc, c->res_smem * wpc, c->stream>>>(net, make_state(c), thr, c->mw);
     PC_CUDA(cudaGetLastError());
     c->launches += 1;
-    PC_CUDA(cudaMemcpyAsync(c->h_g, c->g, sizeof(Global), cudaMemcpyDeviceToHost, c->stream));
   }
+  PC_CUDA(cudaMemcpyAsync(c->h_g, c->g, sizeof(Global), cudaMemcpyDeviceToHost, c->stream));
   PC_CUDA(cudaMemcpyAsync(c->h_cnt, c->cnt, sizeof(Counters) * (n + 1), cudaMemcpyDeviceToHost, c->stream));
   PC_CUDA(cudaStreamSynchronize(c->stream));
   c->polished = static_cast<Global*>(c->h_g)->polished;
@@ -723,6 +792,10 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   c->nE = last.nE_before + last.nsplit + last.npairs;
   c->have_result = true;
   const Global g = *static_cast<Global*>(c->h_g);
+  if (g.error & kErrCorrupt)
+    throw PcError(PC_ERR_CUDA, "a device counter left its capacity (internal error; check " +
+                                   std::to_string(g.diag_site) + " at " + std::to_string(g.diag_n) + ")");
+  if (g.error & kErrVerify) throw NeedsInlinePairing();
   long long degenerate = 0, undecided = 0;
   bool pairing = (g.error & (kErrPairing | kErrProbe)) != 0;
   int pair_at = -1;
@@ -757,6 +830,7 @@ void StateBufs::release(pc_ctx* c) {
   ctx_free(c, SIG);
   ctx_free(c, E);
   ctx_free(c, stage);
+  ctx_free(c, vlist);
   ctx_free(c, table);
   ctx_free(c, tape_pq);
   ctx_free(c, tape_t);
@@ -828,7 +902,7 @@ pc_status pc_create(pc_ctx** out, int device, const pc_options* opt) {
   pc_default_options(&c->opt);
   if (opt) c->opt = *opt;
   if (c->opt.precision < 0 || c->opt.precision > 2 || c->opt.exec < 0 || c->opt.exec > 1 || c->opt.gemm < 0 ||
-      c->opt.gemm > 1) {
+      c->opt.gemm > 1 || c->opt.pairing < 0 || c->opt.pairing > 1) {
     delete c;
     return PC_ERR_INVALID;
   }
@@ -882,7 +956,14 @@ pc_status pc_extract(pc_ctx* c, int L, const int32_t* widths, const double* para
   try {
     PC_CUDA(cudaSetDevice(c->device));
     c->stream = static_cast<cudaStream_t>(stream);
-    run_extract(c, L, widths, params, lo, hi);
+    try {
+      run_extract(c, L, widths, params, lo, hi, c->opt.pairing == PC_PAIR_DEFERRED);
+    } catch (const NeedsInlinePairing&) {
+      // a 64-bit fingerprint collision paired two different 2-faces: extract
+      // again with every pairing verified before it is made
+      c->reruns += 1;
+      run_extract(c, L, widths, params, lo, hi, false);
+    }
     return PC_OK;
   } catch (const PcError& e) {
     cudaGetLastError();
@@ -970,9 +1051,9 @@ pc_status pc_stats(pc_ctx* c, int64_t* out, int n_neurons) {
 
 pc_status pc_diagnostics(pc_ctx* c, int64_t* out, int n) {
   if (!c || !out) return PC_ERR_INVALID;
-  const int64_t v[10] = {c->launches, c->grows, c->polished, c->degenerate, c->undecided,
-                         c->Vcap, c->Ecap, c->Tcap, (int64_t)c->allocated, c->grid_persist};
-  for (int k = 0; k < n && k < 10; ++k) out[k] = v[k];
+  const int64_t v[11] = {c->launches, c->grows, c->polished, c->degenerate, c->undecided, c->Vcap,
+                         c->Ecap,    c->Tcap,  (int64_t)c->allocated, c->grid_persist, c->reruns};
+  for (int k = 0; k < n && k < 11; ++k) out[k] = v[k];
   return PC_OK;
 }
 
@@ -1021,7 +1102,7 @@ constexpr size_t kNaOffEsc = kNaOffZ1 + kNaZBytes;
 constexpr size_t kNaOffExc = kNaOffEsc + na_align(4 * kNaMaxV);
 constexpr size_t kNaOffStage = kNaOffExc + na_align(4 * kNaMaxV);
 constexpr size_t kNaOffTable = kNaOffStage + na_align(16 * kNaMaxE);
-constexpr size_t kNaOffCnt = kNaOffTable + na_align(8 * kNaMaxT);
+constexpr size_t kNaOffCnt = kNaOffTable + na_align(16 * kNaMaxT);
 constexpr size_t kNaOffG = kNaOffCnt + na_align(sizeof(Counters) * (kNaMaxN + 1));
 constexpr size_t kNaOffCta = kNaOffG + na_align(sizeof(Global));
 constexpr size_t kNaBytes = kNaOffCta + na_align(8 * 2 * kMaxGrid);
@@ -1139,7 +1220,7 @@ extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const doub
                                                    reinterpret_cast<float*>(base + kNaOffNorm), p);
     PC_CUDA(cudaGetLastError());
     // the scratch keeps the previous call's contents: reset what must start empty
-    PC_CUDA(cudaMemsetAsync(base + kNaOffTable, 0xff, 8 * kNaMaxT, c.stream));
+    PC_CUDA(cudaMemsetAsync(base + kNaOffTable, 0xff, 16 * kNaMaxT, c.stream));
     PC_CUDA(cudaMemsetAsync(base + kNaOffCnt, 0, sizeof(Counters) * (nn + 1), c.stream));
     c.res_smem = (size_t)newton_ws_doubles(mw, D) * 8;
     occupancy_any(&c);

@@ -37,6 +37,7 @@ struct StateBufs {
   void* SIG = nullptr;
   void* E = nullptr;
   void* stage = nullptr;
+  void* vlist = nullptr;
   void* table = nullptr;
   void* tape_pq = nullptr;
   void* tape_t = nullptr;
@@ -77,6 +78,9 @@ struct pc_ctx {
   void* cta = nullptr;
   void* h_cnt = nullptr;
   void* h_g = nullptr;
+
+  int deferred = 0;  // this extraction pairs by fingerprint (checked after)
+  int reruns = 0;    // extractions repeated with inline face verification
 
   // launch geometry
   int grid_persist = 0, grid_step = 0;

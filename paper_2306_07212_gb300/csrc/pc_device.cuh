@@ -34,6 +34,7 @@ constexpr uint64_t kEvenBits = 0x5555555555555555ull;
 
 constexpr uint64_t kEmpty = ~0ull;       // empty hash slot
 constexpr uint64_t kPaired = 1ull << 31; // payload flag: face already paired
+constexpr unsigned long long kPaired64 = 1ull << 63;  // same, in the 16-byte slots
 
 constexpr int kBlock = 512;              // threads per CTA in the neuron phases
 constexpr int kWarps = kBlock / 32;
@@ -47,6 +48,7 @@ constexpr int kErrTimeout = 4;
 constexpr int kErrProbe = 8;
 constexpr int kErrConflict = 16;
 constexpr int kErrCorrupt = 32;   // a counter outside its capacity: stop, never index with it
+constexpr int kErrVerify = 64;    // a fingerprint pairing failed its exact check (deferred mode)
 constexpr int kErrFatal = kErrTimeout | kErrCorrupt;
 
 // halt reasons
@@ -110,7 +112,9 @@ struct State {
   int32_t* EU;
   int32_t* EW;
   int4* stage;           // splitting edges (edge, V+, V-, 0) staged per CTA range
-  uint64_t* table;
+  uint64_t* table;       // hash slots: 16 bytes (fingerprint, payload), or 8 bytes (tag | payload) inline
+  int4* vlist;           // per edge: (v_a, v_b, zero ordinals, neuron + 1) of a pairing edge, else 0
+  int deferred;          // pairings by 64-bit fingerprint, verified after the extraction
   Counters* cnt;
   Global* g;
   long long* cta_count;
@@ -130,6 +134,21 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   x *= 0x94d049bb133111ebull;
   x ^= x >> 31;
   return x;
+}
+
+// 128-bit compare-and-swap of a 16-byte-aligned slot {lo, hi} (sm_90+).
+__device__ __forceinline__ void cas128(unsigned long long* addr, unsigned long long cmp_lo, unsigned long long cmp_hi,
+                                       unsigned long long new_lo, unsigned long long new_hi,
+                                       unsigned long long& old_lo, unsigned long long& old_hi) {
+  asm volatile(
+      "{\n\t.reg .b128 c, n, d;\n\t"
+      "mov.b128 c, {%2, %3};\n\t"
+      "mov.b128 n, {%4, %5};\n\t"
+      "atom.global.cas.b128 d, [%6], c, n;\n\t"
+      "mov.b128 {%0, %1}, d;\n\t}"
+      : "=l"(old_lo), "=l"(old_hi)
+      : "l"(cmp_lo), "l"(cmp_hi), "l"(new_lo), "l"(new_hi), "l"(addr)
+      : "memory");
 }
 
 __device__ __forceinline__ uint64_t word_hash(int w, uint64_t v) {

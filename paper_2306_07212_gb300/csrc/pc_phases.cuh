@@ -27,14 +27,14 @@
 
 namespace pc {
 
-constexpr int kPairCap = 2048;   // intersecting edges a CTA buffers per step
+constexpr int kPairCap = 1024;   // intersecting edges a CTA buffers per step
 
 struct Smem {
   long long pref[kMaxGrid + 1];
   long long wsum[kWarps + 1];
   long long flist[kFilterCap];
   int zlist[kWarps][32];
-  int2 pairs[kPairCap];
+  int4 pairs[kPairCap];   // (v_partner, v_new, zero ordinals, neuron + 1)
   int npairs;
   int fcount;
   int flip;
@@ -280,7 +280,7 @@ __device__ void phase_classify(const NetDesc& net, const State& st, int zb, int 
     if (threadIdx.x == 0 && sm.flip) atomicMax(&st.g->flip_at, n);
   }
   // the part of the hash table that the previous neuron used
-  const long long tprev = st.cnt[n].tsize;
+  const long long tprev = 2 * st.cnt[n].tsize;  // 16-byte slots (the inline mode uses the first half)
   for (long long t = (long long)blockIdx.x * kBlock + threadIdx.x; t < tprev; t += (long long)gridDim.x * kBlock)
     st.table[t] = kEmpty;
   // step (3): splitting edges, speculatively from the signs of the values
@@ -448,8 +448,8 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
       if (lane == 0) report_corrupt(st.g, 4, n, ed, p, q);
       continue;
     }
-    const double a = static_cast<double>(Z[(long long)i * Vcap + p]);
-    const double b = static_cast<double>(Z[(long long)i * Vcap + q]);
+    // every endpoint load is issued before any of them is used
+    const ZT za0 = Z[(long long)i * Vcap + p], zb0 = Z[(long long)i * Vcap + q];
     double xp = 0.0, xq = 0.0;
     if (lane < D) {
       xp = st.X[(long long)lane * Vcap + p];
@@ -460,6 +460,24 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
       sp = st.SIG[(long long)lane * Vcap + p];
       sq = st.SIG[(long long)lane * Vcap + q];
     }
+    ZT zpa = ZT(0), zqa = ZT(0), zpb = ZT(0), zqb = ZT(0);  // rows lane and lane + 32 of the first 64
+    if (lane < H) {
+      zpa = Z[(long long)lane * Vcap + p];
+      zqa = Z[(long long)lane * Vcap + q];
+    }
+    if (lane + 32 < H) {
+      zpb = Z[(long long)(lane + 32) * Vcap + p];
+      zqb = Z[(long long)(lane + 32) * Vcap + q];
+    }
+    float rp = 0.f, rq = 0.f, xep = 0.f, xeq = 0.f;
+    if (TRACK && lane == 0) {
+      rp = st.esc[p];
+      rq = st.esc[q];
+      xep = st.exc[p];
+      xeq = st.exc[q];
+    }
+    const double a = static_cast<double>(za0);
+    const double b = static_cast<double>(zb0);
     double t = a / (a - b);
     bool bad = !(a > 0.0 && b < 0.0);
     if (!(t >= 0.0 && t <= 1.0)) { t = t < 0.0 ? 0.0 : 1.0; bad = true; }
@@ -470,14 +488,16 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
     float amax = 0.f;
     for (int j0 = 0; j0 < H; j0 += 64) {
       const int ja = j0 + lane, jb = ja + 32;
-      ZT zpa = ZT(0), zqa = ZT(0), zpb = ZT(0), zqb = ZT(0);
-      if (ja < H) {
-        zpa = Z[(long long)ja * Vcap + p];
-        zqa = Z[(long long)ja * Vcap + q];
-      }
-      if (jb < H) {
-        zpb = Z[(long long)jb * Vcap + p];
-        zqb = Z[(long long)jb * Vcap + q];
+      if (j0 > 0) {
+        zpa = zqa = zpb = zqb = ZT(0);
+        if (ja < H) {
+          zpa = Z[(long long)ja * Vcap + p];
+          zqa = Z[(long long)ja * Vcap + q];
+        }
+        if (jb < H) {
+          zpb = Z[(long long)jb * Vcap + p];
+          zqb = Z[(long long)jb * Vcap + q];
+        }
       }
       const ZT za = (ja == i) ? ZT(0) : zpa + tz * (zqa - zpa);
       const ZT zb2 = (jb == i) ? ZT(0) : zpb + tz * (zqb - zpb);
@@ -503,13 +523,12 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
         // in t = a / (a - b), added in quadrature to the endpoints' position
         // estimates (independent errors; the convex combination does not
         // amplify the endpoints' own errors).
-        const float rp = st.esc[p], rq = st.esc[q];
         const float rm = fmaxf(rp, rq), rr = 5.9604645e-8f * amax;
         st.esc[v0] = sqrtf(rm * rm + rr * rr);
         const float ep = nrl[3 * i] * rp + 2.9802322e-8f * nrl[3 * i + 1];
         const float eq = nrl[3 * i] * rq + 2.9802322e-8f * nrl[3 * i + 1];
         const float shift = static_cast<float>((ep + eq) / (a - b)) * dx;
-        const float xe = fmaxf(st.exc[p], st.exc[q]);
+        const float xe = fmaxf(xep, xeq);
         st.exc[v0] = sqrtf(xe * xe + shift * shift);
       }
     }
@@ -531,6 +550,7 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
       st.EW[ed] = v0;
       st.EU[nE + k] = q;
       st.EW[nE + k] = v0;
+      if (st.deferred) st.vlist[nE + k] = make_int4(0, 0, 0, 0);  // not a pairing edge
       if (st.keep_tape) {
         st.tape_pq[v0] = p;
         st.tape_pq[st.tape_cap + v0] = q;
@@ -568,63 +588,105 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
     const bool has_key = (nz == D - 1) && (o < nz) && !(minus && jz < m);
     nkeys_w += __popc(__ballot_sync(0xffffffffu, has_key));
     if (bad) ndeg_w += 1;
-    uint64_t Fw = 0, mine = 0;
-    uint32_t tag = 0;
+    uint64_t Fw = 0, h = 0;
     long long slot = 0;
     if (has_key) {
       Fw = (s0w & ~(3ull << shj)) | ((minus ? kMinus : kPlus) << shj);
-      const uint64_t h = hb ^ word_hash(wj, s0w) ^ word_hash(wj, Fw);
-      tag = uint32_t(h >> 32);
-      mine = (uint64_t(tag) << 32) | (uint64_t(k) * R + uint64_t(lane));
+      h = hb ^ word_hash(wj, s0w) ^ word_hash(wj, Fw);
       slot = (long long)(h & (uint64_t)tmask);
     }
-    bool active = has_key;
-    long long probes = 0;
-    while (__any_sync(0xffffffffu, active)) {
-      bool cand = false;
-      uint64_t old = 0;
-      if (active) {
-        old = atomicCAS(reinterpret_cast<unsigned long long*>(st.table + slot), (unsigned long long)kEmpty,
-                        (unsigned long long)mine);
-        if (old == kEmpty) {
-          active = false;  // first arrival: the partner will pair with it
-        } else if (uint32_t(old >> 32) == tag) {
-          cand = true;
-        } else {
-          slot = (slot + 1) & tmask;
-          if (++probes > tneed) { err_w |= kErrProbe; active = false; }
-        }
-      }
-      unsigned cm = __ballot_sync(0xffffffffu, cand);
-      while (cm) {
-        const int L = __ffs(cm) - 1;
-        cm &= cm - 1;
-        const uint64_t pp = __shfl_sync(0xffffffffu, old, L) & 0x7fffffffull;
-        const int wjL = __shfl_sync(0xffffffffu, wj, L);
-        const uint64_t FwL = __shfl_sync(0xffffffffu, Fw, L);
-        const bool eq = warp_face_matches(st, sm, G, chunk, (long long)(pp / R), int(pp % R), e, S, s0, wjL, FwL,
-                                          nV, total, n);
-        if (lane == L) {
-          if (eq) {
-            const uint64_t prev = atomicOr(reinterpret_cast<unsigned long long*>(st.table + slot),
-                                           (unsigned long long)kPaired);
-            if (prev & kPaired) {
+    if (st.deferred) {
+      // Full 64-bit fingerprint and payload in one 16-byte slot: the first
+      // arrival inserts both with one 128-bit CAS, the second finds the
+      // partner in the same atomic and pairs at once.  Every pairing is
+      // re-checked exactly after the extraction (k_verify_pairs) from the
+      // two new vertices' sign vectors.
+      if (has_key) {
+        if (h == kEmpty) h = kEmpty - 1;
+        const unsigned long long mine = uint64_t(k) * R + uint64_t(lane);
+        unsigned long long* tb = reinterpret_cast<unsigned long long*>(st.table);
+        for (long long probes = 0;; ++probes) {
+          if (probes > tneed) {
+            err_w |= kErrProbe;
+            break;
+          }
+          unsigned long long ok, ov;
+          cas128(tb + 2 * slot, kEmpty, kEmpty, h, mine, ok, ov);
+          if (ok == kEmpty) break;  // first arrival
+          if (ok == h) {
+            const unsigned long long prev = atomicOr(tb + 2 * slot + 1, kPaired64);
+            if (prev & kPaired64) {
               err_w |= kErrPairing;
             } else {
-              const int v2 = int(nV + (long long)(pp / R));
+              const long long k2 = (long long)((ov & ~kPaired64) / R);
+              const int r2 = int((ov & ~kPaired64) % R);
+              const int4 rec = make_int4(int(nV + k2), v0, (r2 << 16) | lane, n + 1);
               const int slot2 = atomicAdd(&sm.npairs, 1);
               if (slot2 < kPairCap) {
-                sm.pairs[slot2] = make_int2(v2, v0);
+                sm.pairs[slot2] = rec;
               } else {
                 const long long idx = atomic_add_ll(&cur->npairs, 1ll);
-                st.EU[nE + total + idx] = v2;
-                st.EW[nE + total + idx] = v0;
+                st.EU[nE + total + idx] = rec.x;
+                st.EW[nE + total + idx] = rec.y;
+                st.vlist[nE + total + idx] = rec;
               }
             }
-            active = false;
+            break;
+          }
+          slot = (slot + 1) & tmask;
+        }
+      }
+    } else {
+      const uint32_t tag = uint32_t(h >> 32);
+      const uint64_t mine = has_key ? ((uint64_t(tag) << 32) | (uint64_t(k) * R + uint64_t(lane))) : 0ull;
+      bool active = has_key;
+      long long probes = 0;
+      while (__any_sync(0xffffffffu, active)) {
+        bool cand = false;
+        uint64_t old = 0;
+        if (active) {
+          old = atomicCAS(reinterpret_cast<unsigned long long*>(st.table + slot), (unsigned long long)kEmpty,
+                          (unsigned long long)mine);
+          if (old == kEmpty) {
+            active = false;  // first arrival: the partner will pair with it
+          } else if (uint32_t(old >> 32) == tag) {
+            cand = true;
           } else {
             slot = (slot + 1) & tmask;
             if (++probes > tneed) { err_w |= kErrProbe; active = false; }
+          }
+        }
+        unsigned cm = __ballot_sync(0xffffffffu, cand);
+        while (cm) {
+          const int L = __ffs(cm) - 1;
+          cm &= cm - 1;
+          const uint64_t pp = __shfl_sync(0xffffffffu, old, L) & 0x7fffffffull;
+          const int wjL = __shfl_sync(0xffffffffu, wj, L);
+          const uint64_t FwL = __shfl_sync(0xffffffffu, Fw, L);
+          const bool eq = warp_face_matches(st, sm, G, chunk, (long long)(pp / R), int(pp % R), e, S, s0, wjL, FwL,
+                                            nV, total, n);
+          if (lane == L) {
+            if (eq) {
+              const uint64_t prev = atomicOr(reinterpret_cast<unsigned long long*>(st.table + slot),
+                                             (unsigned long long)kPaired);
+              if (prev & kPaired) {
+                err_w |= kErrPairing;
+              } else {
+                const int v2 = int(nV + (long long)(pp / R));
+                const int slot2 = atomicAdd(&sm.npairs, 1);
+                if (slot2 < kPairCap) {
+                  sm.pairs[slot2] = make_int4(v2, v0, 0, 0);
+                } else {
+                  const long long idx = atomic_add_ll(&cur->npairs, 1ll);
+                  st.EU[nE + total + idx] = v2;
+                  st.EW[nE + total + idx] = v0;
+                }
+              }
+              active = false;
+            } else {
+              slot = (slot + 1) & tmask;
+              if (++probes > tneed) { err_w |= kErrProbe; active = false; }
+            }
           }
         }
       }
@@ -648,8 +710,10 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
   __syncthreads();
   const long long base = nE + total + sm.acc[2];
   for (int t = threadIdx.x; t < np; t += kBlock) {
-    st.EU[base + t] = sm.pairs[t].x;
-    st.EW[base + t] = sm.pairs[t].y;
+    const int4 rec = sm.pairs[t];
+    st.EU[base + t] = rec.x;
+    st.EW[base + t] = rec.y;
+    if (st.deferred) st.vlist[base + t] = rec;
   }
   return false;
 }

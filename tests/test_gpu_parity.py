@@ -164,3 +164,19 @@ def test_tensor_core_product_matches_simt_and_oracle(cuda, widths):
         perm = np.array([ka[r.tobytes()] for r in np.ascontiguousarray(b.sign_words().T)])
         scale = max(1.0, float(np.max(np.abs(vb))))
         assert float(np.max(np.abs(va[perm] - vb))) <= 1e-4 * scale
+
+
+@pytest.mark.parametrize("D,widths", [(2, [2, 12, 12, 12, 12, 1]), (3, [3, 16, 16, 1]), (4, [4, 12, 12, 1])])
+@pytest.mark.parametrize("execution", ["persistent", "stepwise"])
+def test_inline_and_deferred_pairing_agree_with_oracle(cuda, D, widths, execution):
+    """Step 5 both ways: fingerprint pairing checked after the extraction
+    (default) and pairing verified before it is made."""
+    net = wl.he_normal_mlp(widths, seed=77)
+    box = wl.Box.cube(D)
+    ref = oracle.extract(net, box)
+    for pairing in ("deferred", "inline"):
+        with cuda(precision="mixed", execution=execution, pairing=pairing) as ex:
+            ex.extract(net, box)
+            assert_same_complex(_gpu_triple(ex), (ref.X, ref.S, ref.E), coord_tol=_tol(box),
+                                what=f"{widths} {pairing} {execution}")
+            assert ex.diagnostics()["reruns"] == 0
