@@ -70,10 +70,16 @@ typedef enum {
 } pc_exec;
 
 typedef enum {
-  PC_GEMM_TENSOR = 0,  /* tcgen05 3xTF32 tensor-core product for layers with
-                          widths <= 128 (FP32 and mixed precision), SIMT FP32
-                          otherwise; the first layer (K = D) is always FP64 FMA */
-  PC_GEMM_SIMT = 1     /* SIMT FP32 FMA for every layer */
+  PC_GEMM_TENSOR = 0,        /* tcgen05 tensor-core product for layers with
+                                widths <= 128 (FP32 and mixed precision), SIMT
+                                FP32 otherwise; the first layer (K = D) is
+                                always FP64 FMA.  Operands split in three TF32
+                                pieces (exact for FP32), six MMAs: FP32
+                                accuracy */
+  PC_GEMM_SIMT = 1,          /* SIMT FP32 FMA for every layer */
+  PC_GEMM_TENSOR_3XTF32 = 2  /* tensor cores, two-piece 3xTF32 (three MMAs,
+                                about 22 bits per product; the value error
+                                scale is widened to match) */
 } pc_gemm;
 
 typedef enum {

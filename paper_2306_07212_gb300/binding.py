@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "PC_OK", 1: "PC_ERR_INVALID", 2: "PC_ERR_OOM", 3: "PC_ERR_CUD
                 4: "PC_ERR_DEGENERATE", 5: "PC_ERR_PAIRING", 6: "PC_ERR_TOO_LARGE",
                 7: "PC_ERR_TIMEOUT", 8: "PC_ERR_NO_TAPE", 9: "PC_PENDING"}
 PRECISION = {"fp32": 0, "mixed": 1, "fp64": 2}
-GEMM = {"tensor": 0, "simt": 1}
+GEMM = {"tensor": 0, "simt": 1, "tensor3x": 2}
 PAIRING = {"deferred": 0, "inline": 1}
 EXEC = {"persistent": 0, "stepwise": 1}
 

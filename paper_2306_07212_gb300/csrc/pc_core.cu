@@ -531,8 +531,9 @@ template <typename ZT, bool MIXED>
 struct Kernels {
   static void gemm(pc_ctx* c, const State& st, int l) {
     TimerScope ts(c, 2 * l);
-    if (sizeof(ZT) == 4 && c->opt.gemm == PC_GEMM_TENSOR && pc_gemm_tc_eligible(c->net, l)) {
-      PC_CUDA(pc_gemm_tc_launch(c->net, st, l, (c->Vcap + 127) / 128, c->num_sms, c->stream));
+    if (sizeof(ZT) == 4 && c->opt.gemm != PC_GEMM_SIMT && pc_gemm_tc_eligible(c->net, l)) {
+      const int pieces = c->opt.gemm == PC_GEMM_TENSOR_3XTF32 ? 2 : 3;
+      PC_CUDA(pc_gemm_tc_launch(c->net, st, l, (c->Vcap + 127) / 128, c->num_sms, pieces, c->stream));
       c->launches += 1;
       return;
     }
@@ -902,7 +903,7 @@ pc_status pc_create(pc_ctx** out, int device, const pc_options* opt) {
   pc_default_options(&c->opt);
   if (opt) c->opt = *opt;
   if (c->opt.precision < 0 || c->opt.precision > 2 || c->opt.exec < 0 || c->opt.exec > 1 || c->opt.gemm < 0 ||
-      c->opt.gemm > 1 || c->opt.pairing < 0 || c->opt.pairing > 1) {
+      c->opt.gemm > 2 || c->opt.pairing < 0 || c->opt.pairing > 1) {
     delete c;
     return PC_ERR_INVALID;
   }

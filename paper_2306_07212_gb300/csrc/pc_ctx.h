@@ -21,7 +21,7 @@ pc::State pc_make_state(pc_ctx* c);
 bool pc_gemm_tc_eligible(const pc::NetDesc& net, int l);
 cudaError_t pc_gemm_tc_set_attributes();
 cudaError_t pc_gemm_tc_launch(const pc::NetDesc& net, const pc::State& st, int l, long long vcap_tiles, int num_sms,
-                              cudaStream_t stream);
+                              int pieces, cudaStream_t stream);
 
 struct PcError : std::runtime_error {
   pc_status status;

@@ -2,26 +2,33 @@
 //   Z_l = W_l a + b_l for every current vertex, a_k = z_k of layer l-1 if the
 //   vertex's sign entry for that neuron is + and 0 otherwise (the vertex's own
 //   affine piece, Eq. 4 with the stored activation pattern).
-// on the fifth-generation tensor cores (tcgen05) as a 3xTF32 product: both
-// operands are split into a TF32 head and a TF32 tail, x = x_hi + x_lo, and
-//   D = A_hi B_hi + A_hi B_lo + A_lo B_hi
-// is accumulated in FP32 in tensor memory (the dropped tail x tail term is
-// below 2^-22 relative), which keeps the FP32 accuracy of the value arrays.
+// on the fifth-generation tensor cores (tcgen05) as split-TF32 products
+// accumulated in FP32 in tensor memory.  Both operands are split into TF32
+// pieces, x = x0 + x1 (+ x2), and the products of pieces whose indices sum
+// to at most P - 1 are accumulated:
+//   P = 2 (3xTF32):  A0 B0 + A0 B1 + A1 B0, about 22 bits per product;
+//   P = 3 (default): the six products up to index sum 2; the three-piece
+//                    split is exact for an FP32 input, so the product has
+//                    the FP32 accuracy that the value arrays and their
+//                    error scale assume.
 //
 // Shape of one tile: M = 128 vertices (tensor-memory lanes), N = H_l neurons
 // padded to a multiple of 16 (columns), K = H_{l-1} inputs in chunks of 32.
 // Operands live in shared memory in the K-major 128-byte-swizzle layout: row
 // r of a chunk (a vertex for A, a neuron for B) holds 32 values (128 B); the
 // 16-byte groups of row r are permuted by XOR with r mod 8; 8-row groups are
-// 1024 B apart.  W_l is split and staged once per CTA; activation tiles are
-// gathered from the neuron-major value rows (coalesced over vertices), masked
-// by the sign words, split, and written by the 128 threads (one vertex each).
-// One elected thread issues the MMAs and commits them to an mbarrier; the
-// epilogue reads the accumulator rows back with tcgen05.ld (thread t holds
-// vertex t), adds b_l and stores the value rows, coalesced over vertices,
-// together with the per-vertex FP32 error scale of the layer.
+// 1024 B apart.  The pieces of W_l are split from FP64 and staged once per
+// CTA.  Activation chunks are gathered from the neuron-major value rows
+// (coalesced over vertices), masked by the sign words and split in registers
+// by the 128 threads (one vertex each); each piece goes to one of two
+// shared-memory buffers, so the next piece is written while the MMAs of the
+// previous one run.  One elected thread issues the MMAs and commits them to
+// the buffer's mbarrier; the epilogue reads the accumulator rows back with
+// tcgen05.ld (thread t holds vertex t), adds b_l and stores the value rows,
+// coalesced over vertices, together with the per-vertex error scale.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "pc_ctx.h"
@@ -34,9 +41,12 @@ constexpr int kTcChunkK = 32;    // inputs per 128-byte swizzle row
 constexpr int kTcMaxN = 128;     // widest layer on this path
 constexpr int kTcMaxK = 128;     // widest input on this path
 constexpr int kTcAChunkBytes = kTcTileM * 128;
-// B (head and tail of W^T for all of K) + A (head and tail of one chunk) +
-// 1024 B for aligning the base + 1024 B of slack behind the operands
-constexpr int kTcSmemMax = 2 * (kTcMaxK / kTcChunkK) * kTcMaxN * 128 + 2 * kTcAChunkBytes + 2048;
+// W^T pieces for all of K + two activation buffers (one piece of one chunk
+// each) + 1024 B for aligning the base + 1024 B of slack behind the operands
+__host__ __device__ constexpr int tc_smem_bytes(int pieces, int kc, int npad) {
+  return pieces * kc * npad * 128 + 2 * kTcAChunkBytes + 2048;
+}
+constexpr int kTcSmemMax = tc_smem_bytes(3, kTcMaxK / kTcChunkK, kTcMaxN);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -123,9 +133,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
   for (int q = 0; q < 16; ++q) r[q] = __uint_as_float(u[q]);
 }
 
+// PIECES = 2: the 3xTF32 product (head x head + head x tail + tail x head);
+// each product keeps about 22 bits.  PIECES = 3: a three-piece split
+// (x = x0 + x1 + x2, which is exact for an FP32 x), with the six products
+// whose piece indices sum to at most 2; each product keeps about 33 bits,
+// so the result has the FP32 accuracy of the SIMT product.
+//
+// Accumulation.  The tensor core adds each MMA's result to its FP32
+// accumulator with a rounding that does not average out over many adds
+// (measured: coordinate errors grew in proportion to the MMAs per
+// accumulator).  So every K step (8 inputs) gets its own accumulator while
+// tensor memory allows (512 columns: 8 accumulators of 64 columns, 4 of 128),
+// the products of a step are issued from the smallest to the largest (tail
+// pieces first, head x head last), and the epilogue sums the accumulators
+// with FP32 round-to-nearest adds.
+template <int PIECES>
 __global__ void __launch_bounds__(kTcTileM, 1) k_gemm_tc(NetDesc net, State st, int l, int Npad, int Kpad) {
   extern __shared__ unsigned char tc_raw[];
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bar[2];
   __shared__ uint32_t tmem_base;
   __shared__ float bias[kTcMaxN];
   __shared__ int fail;
@@ -141,30 +166,35 @@ __global__ void __launch_bounds__(kTcTileM, 1) k_gemm_tc(NetDesc net, State st, 
   const uint32_t chunkB = static_cast<uint32_t>(Npad) * 128u;
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) &
                                                          ~static_cast<uintptr_t>(1023));
-  unsigned char* Bhi = base;
-  unsigned char* Blo = Bhi + KC * chunkB;
-  unsigned char* Ahi = Blo + KC * chunkB;
-  unsigned char* Alo = Ahi + kTcAChunkBytes;
+  unsigned char* Bp = base;                         // [piece][chunk][Npad rows][128 B]
+  unsigned char* Abuf = Bp + PIECES * KC * chunkB;  // two buffers of one chunk piece
 
-  // W^T (rows: neurons, K-major), split into TF32 head and tail from FP64
+  // W^T (rows: neurons, K-major), split into TF32 pieces from FP64
   const double* W = net.W64 + net.wofs[l];
   for (int idx = tid; idx < Npad * Kpad; idx += blockDim.x) {
     const int j = idx / Kpad, k = idx % Kpad;
-    const double w = (j < H && k < K) ? W[(long long)j * K + k] : 0.0;
-    const uint32_t hi = to_tf32(static_cast<float>(w));
-    const uint32_t lo = to_tf32(static_cast<float>(w - static_cast<double>(__uint_as_float(hi))));
+    double r = (j < H && k < K) ? W[(long long)j * K + k] : 0.0;
     const uint32_t off = (k / kTcChunkK) * chunkB + sw128_offset(j, k % kTcChunkK);
-    *reinterpret_cast<uint32_t*>(Bhi + off) = hi;
-    *reinterpret_cast<uint32_t*>(Blo + off) = lo;
+#pragma unroll
+    for (int pc = 0; pc < PIECES; ++pc) {
+      const uint32_t w = to_tf32(static_cast<float>(r));
+      *reinterpret_cast<uint32_t*>(Bp + pc * KC * chunkB + off) = w;
+      r -= static_cast<double>(__uint_as_float(w));
+    }
   }
   for (int j = tid; j < kTcMaxN; j += blockDim.x)
     bias[j] = j < H ? static_cast<float>(net.W64[net.bofs[l] + j]) : 0.f;
   if (tid == 0) {
     fail = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])) : "memory");
   }
-  int ncols = 32;
-  while (ncols < Npad) ncols <<= 1;
+  int stride = 32;  // columns per accumulator (a power of two >= Npad)
+  while (stride < Npad) stride <<= 1;
+  const int ksteps = Kpad / 8;
+  int nacc = 1;
+  while (nacc * 2 <= ksteps && nacc * 2 * stride <= 512) nacc <<= 1;
+  const int ncols = nacc * stride;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                  "r"(ncols)
@@ -181,67 +211,105 @@ __global__ void __launch_bounds__(kTcTileM, 1) k_gemm_tc(NetDesc net, State st, 
   const float* Zin = static_cast<const float*>(st.Z[l - 1]);
   float* Zout = static_cast<float*>(st.Z[l]);
   const int ebase = net.m + net.off[l - 1];
-  uint32_t phase = 0;
+  // buffer b's MMAs: committed (pending[b]) and the parity of their phase
+  uint32_t parity[2] = {0u, 0u};
+  int pending[2] = {0, 0};
+  int stage = 0;  // A buffer to fill next
 
   for (long long tile = blockIdx.x; tile * kTcTileM < nV; tile += gridDim.x) {
     const long long v = tile * kTcTileM + tid;
     const bool valid = v < nV;
     float a2 = 0.f;
-    for (int q = 0; q < KC; ++q) {
-      // gather, mask and split this vertex's 32 inputs of chunk q
+    for (int q = 0; q < KC && !fail; ++q) {
+      // this vertex's 32 inputs of chunk q, masked by its activation pattern
+      float x[kTcChunkK];
       uint64_t word = 0;
       int cw = -1;
 #pragma unroll
-      for (int g = 0; g < kTcChunkK / 4; ++g) {
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int k = q * kTcChunkK + g * 4 + e;
-          float a = 0.f;
-          if (valid && k < K) {
-            const int entry = ebase + k, wi = entry >> 5;
-            if (wi != cw) {
-              word = st.SIG[(long long)wi * Vcap + v];
-              cw = wi;
-            }
-            if (((word >> (2 * (entry & 31))) & 3ull) == kPlus) a = Zin[(long long)k * Vcap + v];
+      for (int k0 = 0; k0 < kTcChunkK; ++k0) {
+        const int k = q * kTcChunkK + k0;
+        float a = 0.f;
+        if (valid && k < K) {
+          const int entry = ebase + k, wi = entry >> 5;
+          if (wi != cw) {
+            word = st.SIG[(long long)wi * Vcap + v];
+            cw = wi;
           }
-          a2 = fmaf(a, a, a2);
-          hi[e] = to_tf32(a);
-          lo[e] = to_tf32(a - __uint_as_float(hi[e]));
+          if (((word >> (2 * (entry & 31))) & 3ull) == kPlus) a = Zin[(long long)k * Vcap + v];
         }
-        const uint32_t off = sw128_offset(tid, g * 4);
-        *reinterpret_cast<uint4*>(Ahi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(Alo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        a2 = fmaf(a, a, a2);
+        x[k0] = a;
       }
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      if (tid == 0) {
-        const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
-        const uint32_t bh = smem_u32(Bhi + q * chunkB), bl = smem_u32(Blo + q * chunkB);
+      for (int pa = PIECES - 1; pa >= 0; --pa) {  // tail pieces first
+        const int b = stage;
+        stage ^= 1;
+        // the buffer is free once the MMAs that read it have completed
+        if (pending[b]) {
+          if (!mbar_wait(&bar[b], parity[b])) fail = 1;
+          parity[b] ^= 1u;
+          pending[b] = 0;
+        }
+        unsigned char* A = Abuf + b * kTcAChunkBytes;
 #pragma unroll
-        for (int kk = 0; kk < kTcChunkK / 8; ++kk) {  // 8 TF32 (32 B) per MMA
-          const uint32_t o = kk * 32;
-          mma_tf32(tmem, sw128_desc(al + o), sw128_desc(bh + o), idesc, (q > 0 || kk > 0) ? 1 : 0);
-          mma_tf32(tmem, sw128_desc(ah + o), sw128_desc(bl + o), idesc, 1);
-          mma_tf32(tmem, sw128_desc(ah + o), sw128_desc(bh + o), idesc, 1);
+        for (int g = 0; g < kTcChunkK / 4; ++g) {
+          uint32_t u[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {  // piece pa of x: split again from the value
+            float r = x[g * 4 + e];
+            uint32_t pc = to_tf32(r);
+#pragma unroll
+            for (int k = 0; k < PIECES - 1; ++k)
+              if (k < pa) {
+                r -= __uint_as_float(pc);
+                pc = to_tf32(r);
+              }
+            u[e] = pc;
+          }
+          *reinterpret_cast<uint4*>(A + sw128_offset(tid, g * 4)) = make_uint4(u[0], u[1], u[2], u[3]);
         }
-        mma_commit(&bar);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0 && !fail) {
+          const uint32_t aa = smem_u32(A);
+#pragma unroll
+          for (int kk = 0; kk < kTcChunkK / 8; ++kk) {  // 8 TF32 (32 B) per MMA
+            const uint32_t o = kk * 32;
+            const int s = q * (kTcChunkK / 8) + kk;
+            const uint32_t dacc = tmem + static_cast<uint32_t>((s % nacc) * stride);
+            for (int pw = PIECES - 1 - pa; pw >= 0; --pw) {  // smallest products first
+              // the first product into an accumulator overwrites it
+              const bool fresh = s < nacc && pa == PIECES - 1 && pw == 0;
+              const uint32_t bb = smem_u32(Bp + (pw * KC + q) * chunkB);
+              mma_tf32(dacc, sw128_desc(aa + o), sw128_desc(bb + o), idesc, fresh ? 0 : 1);
+            }
+          }
+          mma_commit(&bar[b]);
+        }
+        pending[b] = 1;
       }
-      __syncwarp();
-      // the chunk buffers are rewritten next: wait until the MMAs have read them
-      if (!mbar_wait(&bar, phase)) fail = 1;
-      phase ^= 1u;
-      tc_fence_after();
       if (__syncthreads_or(fail)) break;
     }
-    if (fail) break;
+    // all of this tile's MMAs complete before the accumulator is read
+    for (int b = 0; b < 2; ++b)
+      if (pending[b]) {
+        if (!mbar_wait(&bar[b], parity[b])) fail = 1;
+        parity[b] ^= 1u;
+        pending[b] = 0;
+      }
+    tc_fence_after();
+    if (__syncthreads_or(fail)) break;
     // epilogue: accumulator row tid -> value rows of layer l (+ b_l)
     for (int j0 = 0; j0 < Npad; j0 += 16) {
       float r[16];
       tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(j0), r);
+      for (int ia = 1; ia < nacc && ia < ksteps; ++ia) {
+        float r2[16];
+        tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(ia * stride + j0), r2);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) r[jj] += r2[jj];
+      }
       if (valid) {
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj)
@@ -249,10 +317,14 @@ __global__ void __launch_bounds__(kTcTileM, 1) k_gemm_tc(NetDesc net, State st, 
       }
     }
     if (valid) {
-      // FP32 error scale of the layer's values: u/2 ||a||_2 for the
-      // rounding, and the previous layer's scale carried through W_{l-1}
+      // error scale of the layer's values: the rounding of the product
+      // (u/2 ||a||_2 for FP32 accuracy; 2^-21 ||a||_2 for 3xTF32, whose
+      // products keep about 22 bits) and the previous layer's scale carried
+      // through W_{l-1}
+      // (several K steps sharing an accumulator add one rounding each)
       const float u = 5.9604645e-8f;  // 2^-24
-      float rho = 0.5f * u * sqrtf(a2);
+      const float share = static_cast<float>((ksteps + nacc - 1) / nacc);
+      float rho = (PIECES == 2 ? 8.f * u : 0.5f * u * share) * sqrtf(a2);
       const float inh = net.norms[2 * (l - 1)] * st.esc[v] + 0.5f * u * net.norms[2 * (l - 1) + 1];
       rho = sqrtf(rho * rho + inh * inh);
       st.esc[v] = rho;
@@ -262,8 +334,13 @@ __global__ void __launch_bounds__(kTcTileM, 1) k_gemm_tc(NetDesc net, State st, 
     __syncthreads();
     tc_fence_after();
   }
+  // nothing may still read shared memory or write tensor memory at exit
+  for (int b = 0; b < 2; ++b)
+    if (pending[b] && !mbar_wait(&bar[b], parity[b])) fail = 1;
   if (fail && tid == 0) atomicOr(&st.g->error, kErrTimeout);
+  tc_fence_before();
   __syncthreads();
+  tc_fence_after();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
   }
@@ -280,16 +357,28 @@ bool pc_gemm_tc_eligible(const NetDesc& net, int l) {
 }
 
 cudaError_t pc_gemm_tc_set_attributes() {
-  return cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax);
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax);
+  const cudaError_t e2 = cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax);
+  return e != cudaSuccess ? e : e2;
 }
 
 cudaError_t pc_gemm_tc_launch(const NetDesc& net, const State& st, int l, long long vcap_tiles, int num_sms,
-                              cudaStream_t stream) {
+                              int pieces, cudaStream_t stream) {
   const int H = net.w[l + 1], K = net.w[l];
   const int Npad = (H + 15) / 16 * 16;
   const int Kpad = (K + kTcChunkK - 1) / kTcChunkK * kTcChunkK;
-  const size_t smem = static_cast<size_t>(2 * (Kpad / kTcChunkK) * Npad * 128 + 2 * kTcAChunkBytes + 2048);
-  const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>(num_sms, vcap_tiles)));
-  k_gemm_tc<<<grid, kTcTileM, smem, stream>>>(net, st, l, Npad, Kpad);
+  const size_t smem = static_cast<size_t>(tc_smem_bytes(pieces, Kpad / kTcChunkK, Npad));
+  // CTAs per SM that shared and tensor memory allow (the kernel allocates
+  // accumulators up to 512 columns; a CTA waits in tcgen05.alloc while
+  // another CTA on its SM holds the columns)
+  int stride = 32;
+  while (stride < Npad) stride <<= 1;
+  int nacc = 1;
+  while (nacc * 2 <= Kpad / 8 && nacc * 2 * stride <= 512) nacc <<= 1;
+  const int tmem_per_sm = 512 / (nacc * stride);
+  const int per_sm = std::max(1, std::min({4, tmem_per_sm, static_cast<int>(228 * 1024 / (smem + 1024))}));
+  const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>((long long)num_sms * per_sm, vcap_tiles)));
+  if (pieces == 3) k_gemm_tc<3><<<grid, kTcTileM, smem, stream>>>(net, st, l, Npad, Kpad);
+  else k_gemm_tc<2><<<grid, kTcTileM, smem, stream>>>(net, st, l, Npad, Kpad);
   return cudaGetLastError();
 }

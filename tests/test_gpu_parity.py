@@ -144,16 +144,18 @@ def test_context_keeps_its_buffer_shape_through_growth(cuda):
 
 
 @pytest.mark.parametrize("widths", [[3, 64, 64, 64, 1], [2, 16, 128, 40, 8, 1], [4, 32, 96, 1]])
-def test_tensor_core_product_matches_simt_and_oracle(cuda, widths):
-    """The tcgen05 3xTF32 layer product (default) and the SIMT FP32 product
-    give the oracle's complex; their final-layer values agree to FP32 accuracy."""
+@pytest.mark.parametrize("gemm", ["tensor", "tensor3x"])
+def test_tensor_core_product_matches_simt_and_oracle(cuda, widths, gemm):
+    """The tcgen05 layer products (three-piece split, the default, and
+    3xTF32) and the SIMT FP32 product give the oracle's complex; their
+    final-layer values agree to FP32 accuracy."""
     net = wl.he_normal_mlp(widths, seed=11)
     box = wl.Box.cube(widths[0])
     ref = oracle.extract(net, box)
-    with cuda(precision="mixed", gemm="tensor") as a, cuda(precision="mixed", gemm="simt") as b:
+    with cuda(precision="mixed", gemm=gemm) as a, cuda(precision="mixed", gemm="simt") as b:
         a.extract(net, box)
         b.extract(net, box)
-        for ex, name in ((a, "tensor"), (b, "simt")):
+        for ex, name in ((a, gemm), (b, "simt")):
             assert_same_complex(_gpu_triple(ex), (ref.X, ref.S, ref.E), coord_tol=_tol(box), what=f"{widths} {name}")
         assert a.diagnostics()["launches"] > 0
         va, vb = a.values(), b.values()
