@@ -20,13 +20,32 @@ namespace pc {
 // ---------------------------------------------------------------------------
 // Set-up kernels
 
+// The (head, remainder) pairs follow the float32 heads at an even float
+// offset, so that every pair is 8-byte aligned.
+__host__ __device__ inline long long pairs_offset(long long n_params) { return (n_params + 1) & ~1ll; }
+
 // float32 copy of the parameters, and the norms used by the FP32 error
 // estimate: per layer max_j ||W_j||_2 and max_j |b_j|, per neuron ||W_n||_2,
 // |b_n| and 1/||W_n||_2 (rounded outward).
 __global__ void k_prep(NetDesc net, float* W32, float* norms, long long n_params) {
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n_params;
        t += (long long)gridDim.x * blockDim.x)
-    W32[t] = static_cast<float>(net.W64[t]);
+  {
+    const double w = net.W64[t];
+    const float h = static_cast<float>(w);
+    W32[t] = h;
+    // (head, remainder) pair, weights transposed to [K][H] within their layer
+    int l = 0;
+    while (l + 1 < net.L && t >= net.wofs[l + 1]) ++l;
+    long long dst = t;
+    if (t < net.bofs[l]) {
+      const long long e = t - net.wofs[l];
+      const int K = net.w[l], H = net.w[l + 1];
+      dst = net.wofs[l] + (e % K) * H + e / K;
+    }
+    reinterpret_cast<float2*>(W32 + pairs_offset(n_params))[dst] =
+        make_float2(h, static_cast<float>(w - static_cast<double>(h)));
+  }
   if (blockIdx.x < net.L) {
     const int l = blockIdx.x, H = net.w[l + 1], K = net.w[l];
     __shared__ double s_w[256], s_b[256];
@@ -297,12 +316,15 @@ __global__ void __launch_bounds__(256) k_verify_pairs(NetDesc net, State st) {
 }
 
 // Coordinate polish: every vertex whose coordinate error estimate (rms)
-// exceeds thr is moved to its exact position by an FP64 Newton step
-// on its D zero entries (all entries are processed at this point).  One warp
-// per vertex; vertices are dealt to warps round-robin.
-__global__ void __launch_bounds__(kBlock) k_polish(NetDesc net, State st, float thr, int mw) {
+// exceeds thr is moved to its exact position by a Newton step on its D zero
+// entries (all entries are processed at this point), with the values in
+// float-float arithmetic (newton_ff_warp).  One warp per vertex; vertices are
+// dealt to warps round-robin.  n_stage: parameter pairs copied to shared
+// memory (all of them, or 0 when they do not fit; then they are read from
+// global memory, coalesced per layer).
+__global__ void __launch_bounds__(kBlock) k_polish(NetDesc net, State st, float thr, int mw, long long n_stage) {
   // blockDim.x = 32 x (warps whose workspace fits kPolishSmemMax)
-  extern __shared__ double dsm[];
+  extern __shared__ __align__(16) unsigned char psm[];
   __shared__ int zl[kWarps][kMaxD + 2];
   __shared__ NewtonOut nout[kWarps];
   if (cta_stopped(st)) return;
@@ -310,7 +332,11 @@ __global__ void __launch_bounds__(kBlock) k_polish(NetDesc net, State st, float 
   const long long nV = last->nV_before + last->nsplit;
   const long long Vcap = st.Vcap;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* ws = dsm + (long long)warp * newton_ws_doubles(mw, net.D);
+  float2* Ps = reinterpret_cast<float2*>(psm);
+  for (long long t = threadIdx.x; t < n_stage; t += blockDim.x) Ps[t] = net.WT2[t];
+  __syncthreads();
+  const float2* P = n_stage > 0 ? Ps : net.WT2;
+  unsigned char* ws = psm + ((n_stage * 8 + 15) / 16) * 16 + (long long)warp * ff_ws_bytes(mw, net.D);
   long long npol = 0;
   const int wpc = blockDim.x >> 5;
   const long long nwarps = (long long)gridDim.x * wpc;
@@ -321,7 +347,7 @@ __global__ void __launch_bounds__(kBlock) k_polish(NetDesc net, State st, float 
       const int L = __ffs(flag) - 1;
       flag &= flag - 1;
       const long long u = base + L;
-      newton_group<true>(net, st, u, net.P, -1, -1, mw, ws, zl[warp], &nout[warp]);
+      newton_ff_warp(net, st, P, u, net.P, mw, ws, zl[warp], &nout[warp]);
       if (nout[warp].ok) {
         if (lane < net.D) st.X[(long long)lane * Vcap + u] += nout[warp].dlt[lane];
         npol += (lane == 0);
@@ -604,6 +630,13 @@ static int occupancy_any(pc_ctx* c) {
   }
 }
 
+// Parameter pairs the polish keeps in shared memory: all p (8 B each) when
+// they leave room for at least 8 warp workspaces, else none.
+static long long polish_stage(long long p, size_t ws) {
+  const long long bytes = (p * 8 + 15) / 16 * 16;
+  return bytes + 8 * (long long)ws <= kPolishSmemMax ? p : 0;
+}
+
 // Thrown when the exact check after a fingerprint-paired extraction fails.
 struct NeedsInlinePairing {};
 
@@ -665,7 +698,7 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     ctx_free(c, c->params32);
     ctx_free(c, c->norms);
     c->params64 = ctx_alloc(c, pbytes);
-    c->params32 = ctx_alloc(c, sizeof(float) * p);
+    c->params32 = ctx_alloc(c, sizeof(float) * (pairs_offset(p) + 2 * p));  // heads, then (head, remainder) pairs
     c->norms = ctx_alloc(c, sizeof(float) * (2 * kMaxL + 3 * (size_t)n));
     if (!c->params64 || !c->params32 || !c->norms) {
       ctx_free(c, c->params64);
@@ -679,6 +712,7 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   PC_CUDA(cudaMemcpyAsync(c->params64, params, pbytes, cudaMemcpyDefault, c->stream));
   net.W64 = static_cast<const double*>(c->params64);
   net.W32 = static_cast<const float*>(c->params32);
+  net.WT2 = reinterpret_cast<const float2*>(net.W32 + pairs_offset(p));
   net.norms = static_cast<const float*>(c->norms);
   net.nrm = net.norms + 2 * kMaxL;
   k_prep<<<std::max(L, 64), 256, 0, c->stream>>>(net, static_cast<float*>(c->params32), static_cast<float*>(c->norms), p);
@@ -769,9 +803,12 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     double diam = 0.0;
     for (int d = 0; d < D; ++d) diam += (hi[d] - lo[d]) * (hi[d] - lo[d]);
     const float thr = static_cast<float>((c->opt.polish_tol > 0 ? c->opt.polish_tol : 1e-6) * std::sqrt(diam));
-    const int wpc = std::max(1, std::min(kWarps, int(kPolishSmemMax / c->res_smem)));
+    const size_t ws = ff_ws_bytes(c->mw, D);
+    const long long n_stage = polish_stage(p, ws);
+    const size_t stage_b = (n_stage * 8 + 15) / 16 * 16;
+    const int wpc = std::max(1, std::min(kWarps, int((kPolishSmemMax - stage_b) / ws)));
     TimerScope ts(c, pc_ctx::kPolishSlot);
-    k_polish<<<c->grid_step, 32 * wpc, c->res_smem * wpc, c->stream>>>(net, make_state(c), thr, c->mw);
+    k_polish<<<c->grid_step, 32 * wpc, stage_b + ws * wpc, c->stream>>>(net, make_state(c), thr, c->mw, n_stage);
     PC_CUDA(cudaGetLastError());
     c->launches += 1;
   }
@@ -1095,7 +1132,7 @@ constexpr long long kNaMaxParams = 16384;   // float64 parameters
 constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t kNaOffP64 = 0;
 constexpr size_t kNaOffP32 = kNaOffP64 + na_align(8 * kNaMaxParams);
-constexpr size_t kNaOffNorm = kNaOffP32 + na_align(4 * kNaMaxParams);
+constexpr size_t kNaOffNorm = kNaOffP32 + na_align(12 * kNaMaxParams + 8);
 constexpr size_t kNaOffZ0 = kNaOffNorm + na_align(4 * (2 * kMaxL + 3 * kNaMaxN));
 constexpr size_t kNaZBytes = na_align(8ull * kNaMaxWidth * kNaMaxV);
 constexpr size_t kNaOffZ1 = kNaOffZ0 + kNaZBytes;
@@ -1195,6 +1232,7 @@ extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const doub
     }
     net.W64 = reinterpret_cast<const double*>(base + kNaOffP64);
     net.W32 = reinterpret_cast<const float*>(base + kNaOffP32);
+    net.WT2 = reinterpret_cast<const float2*>(net.W32 + pairs_offset(p));
     net.norms = reinterpret_cast<const float*>(base + kNaOffNorm);
     net.nrm = net.norms + 2 * kMaxL;
     c.hmax = hmax;
@@ -1233,8 +1271,11 @@ extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const doub
       double diam = 0.0;
       for (int d = 0; d < D; ++d) diam += (hi[d] - lo[d]) * (hi[d] - lo[d]);
       const float thr = static_cast<float>(c.opt.polish_tol * std::sqrt(diam));
-      const int wpc = std::max(1, std::min(kWarps, int(kPolishSmemMax / c.res_smem)));
-      k_polish<<<c.grid_step, 32 * wpc, c.res_smem * wpc, c.stream>>>(net, make_state(&c), thr, c.mw);
+      const size_t ws = ff_ws_bytes(c.mw, D);
+      const long long n_stage = polish_stage(p, ws);
+      const size_t stage_b = (n_stage * 8 + 15) / 16 * 16;
+      const int wpc = std::max(1, std::min(kWarps, int((kPolishSmemMax - stage_b) / ws)));
+      k_polish<<<c.grid_step, 32 * wpc, stage_b + ws * wpc, c.stream>>>(net, make_state(&c), thr, c.mw, n_stage);
       PC_CUDA(cudaGetLastError());
     }
     Global g{};

@@ -64,6 +64,8 @@ struct NetDesc {
   double lo[kMaxD], hi[kMaxD];
   const double* W64;     // flat parameters, float64 (device copy)
   const float* W32;      // flat parameters rounded to float32
+  const float2* WT2;     // per layer W^T (k-major: [K][H]) then b, as (float32 head,
+                         // float32 of the remainder): about 48 bits per parameter
   const float* norms;    // per layer: [2l] = max_j ||W_j||_2, [2l+1] = max_j |b_j|
   const float* nrm;      // per neuron n: [3n] = ||W_n||_2, [3n+1] = |b_n|, [3n+2] = 1/||W_n||_2
   float kappa;           // filter factor

@@ -23,7 +23,7 @@ __host__ __device__ constexpr int newton_ws_doubles(int mw, int D) {
 // Upper bounds of the dynamic shared memory of the kernels that use the
 // Newton workspace; the launch attributes are set once to these constants.
 constexpr int kNewtonSmemMax = newton_ws_doubles(kMaxWidth, kMaxD) * 8;
-constexpr int kPolishSmemMax = 160 * 1024;
+constexpr int kPolishSmemMax = 220 * 1024;
 
 struct NewtonOut {
   double z;             // value of the target neuron at the exact vertex
@@ -34,6 +34,52 @@ struct NewtonOut {
   int l_last;
   int pad;
 };
+
+// One Newton step on the D zero entries of vertex v: rows are the facets'
+// (+-e_d, value from the stored coordinate) and the neurons' (gradient A,
+// value gv); Gaussian elimination with partial pivoting in float64.
+__device__ inline void newton_solve(const NetDesc& net, const State& st, long long v, const int* s_zl, int nz,
+                                    const double* A, const double* gv, NewtonOut& o) {
+  const int D = net.D, m = net.m;
+  o.ok = 0;
+  if (nz != D) return;
+  double M[kMaxD][kMaxD + 1];
+  for (int q = 0; q < D; ++q) {
+    const int j = s_zl[q];
+    if (j < m) {
+      const int d = j >> 1;
+      const double xd = st.X[(long long)d * st.Vcap + v];
+      for (int dd = 0; dd < D; ++dd) M[q][dd] = 0.0;
+      M[q][d] = (j & 1) ? -1.0 : 1.0;
+      M[q][D] = -((j & 1) ? (net.hi[d] - xd) : (xd - net.lo[d]));
+    } else {
+      for (int dd = 0; dd < D; ++dd) M[q][dd] = A[q * D + dd];
+      M[q][D] = -gv[q];
+    }
+  }
+  for (int c = 0; c < D; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < D; ++r)
+      if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
+    if (M[piv][c] == 0.0) return;
+    if (piv != c)
+      for (int k2 = 0; k2 <= D; ++k2) {
+        const double t = M[c][k2];
+        M[c][k2] = M[piv][k2];
+        M[piv][k2] = t;
+      }
+    for (int r = c + 1; r < D; ++r) {
+      const double f = M[r][c] / M[c][c];
+      for (int k2 = c; k2 <= D; ++k2) M[r][k2] -= f * M[c][k2];
+    }
+  }
+  for (int r = D - 1; r >= 0; --r) {
+    double acc = M[r][D];
+    for (int k2 = r + 1; k2 < D; ++k2) acc -= M[r][k2] * o.dlt[k2];
+    o.dlt[r] = acc / M[r][r];
+  }
+  o.ok = 1;
+}
 
 // v: vertex; e_end: entries < e_end are processed (the zero set is taken among
 // them); l_last: last layer to evaluate (-1: the highest layer of the zero
@@ -167,55 +213,155 @@ __device__ void newton_group(const NetDesc& net, const State& st, long long v, i
     o.l_last = l_last;
     o.z = misc[0];
     o.scale = misc[1];
-    if (nz == D) {
-      double M[kMaxD][kMaxD + 1];
-      for (int q = 0; q < D; ++q) {
-        const int j = s_zl[q];
-        if (j < m) {
-          const int d = j >> 1;
-          const double xd = st.X[(long long)d * Vcap + v];
-          for (int dd = 0; dd < D; ++dd) M[q][dd] = 0.0;
-          M[q][d] = (j & 1) ? -1.0 : 1.0;
-          M[q][D] = -((j & 1) ? (net.hi[d] - xd) : (xd - net.lo[d]));
-        } else {
-          for (int dd = 0; dd < D; ++dd) M[q][dd] = A[q * D + dd];
-          M[q][D] = -gv[q];
-        }
-      }
-      bool ok = true;
-      for (int c = 0; c < D && ok; ++c) {
-        int piv = c;
-        for (int r = c + 1; r < D; ++r)
-          if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
-        if (M[piv][c] == 0.0) {
-          ok = false;
-          break;
-        }
-        if (piv != c)
-          for (int k2 = 0; k2 <= D; ++k2) {
-            const double t = M[c][k2];
-            M[c][k2] = M[piv][k2];
-            M[piv][k2] = t;
-          }
-        for (int r = c + 1; r < D; ++r) {
-          const double f = M[r][c] / M[c][c];
-          for (int k2 = c; k2 <= D; ++k2) M[r][k2] -= f * M[c][k2];
-        }
-      }
-      if (ok) {
-        for (int r = D - 1; r >= 0; --r) {
-          double acc = M[r][D];
-          for (int k2 = r + 1; k2 < D; ++k2) acc -= M[r][k2] * o.dlt[k2];
-          o.dlt[r] = acc / M[r][r];
-        }
-        if (i_target >= 0)
-          for (int dd = 0; dd < D; ++dd) o.z += jt[dd] * o.dlt[dd];
-        o.ok = 1;
-      }
-    }
+    newton_solve(net, st, v, s_zl, nz, A, gv, o);
+    if (o.ok && i_target >= 0)
+      for (int dd = 0; dd < D; ++dd) o.z += jt[dd] * o.dlt[dd];
     *out = o;
   }
   if (WARP) __syncwarp(); else __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Float-float evaluation for the coordinate polish.
+//
+// A value is the unevaluated sum hi + lo of two floats.  Dot products use
+// the compensated scheme of Ogita, Rump and Oishi ("Accurate sum and dot
+// product", 2005, Dot2): each product is split exactly with the FMA
+// (p = a*b, e = fma(a, b, -p)), each addition of p to the running sum is
+// split exactly with Knuth's TwoSum, and the error terms (plus the cross
+// terms of the low parts) are summed in a float, which is as accurate as a
+// dot product in twice the working precision (about 2^-44 of the sum of
+// |terms| here).  Parameters come as (hi = float(w), lo = float(w - hi))
+// pairs, inputs as hi = float(x), lo = float(x - hi).  On GB300 the FP32
+// pipes run about 64x faster than the FP64 units.
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {  // Dekker; |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+
+__host__ __device__ constexpr int ff_ws_bytes(int mw, int D) {
+  // a_hi, a_lo, an_hi, an_lo [mw]; J, Jn [mw x D] (float); then A [D x D],
+  // gv [D] (double) and the sign words
+  return ((4 * mw + 2 * mw * D + 1) / 2 * 2) * 4 + (D * D + D) * 8 + kMaxWords * 8;
+}
+
+// One warp: the Newton step of vertex v on its zero set (entries < e_end),
+// values in float-float, gradients in float32.  P: the (head, remainder)
+// parameters in the WT2 layout, in global or shared memory.  ws:
+// ff_ws_bytes(mw, D) bytes of shared memory private to the warp, 8-byte
+// aligned; s_zl: kMaxD + 2 ints.
+__device__ void newton_ff_warp(const NetDesc& net, const State& st, const float2* P, long long v, int e_end,
+                               int mw, unsigned char* ws, int* s_zl, NewtonOut* out) {
+  const int lane = threadIdx.x & 31;
+  const int D = net.D, m = net.m;
+  const long long Vcap = st.Vcap;
+  float* ahi = reinterpret_cast<float*>(ws);
+  float* alo = ahi + mw;
+  float* nhi = alo + mw;
+  float* nlo = nhi + mw;
+  float* J = nlo + mw;
+  float* Jn = J + mw * D;
+  double* A = reinterpret_cast<double*>(ws + ((4 * mw + 2 * mw * D + 1) / 2 * 2) * 4);
+  double* gv = A + D * D;
+  uint64_t* sig = reinterpret_cast<uint64_t*>(gv + D);
+  {
+    const uint64_t word = lane < net.S ? st.SIG[(long long)lane * Vcap + v] : 0ull;
+    if (lane < net.S) sig[lane] = word;
+    const uint64_t zm = lane < net.S ? zero_mask(word, lane, e_end) : 0ull;
+    const int c = __popcll(zm);
+    int x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    int k = x - c;
+    uint64_t mm = zm;
+    while (mm) {
+      const int bit = __ffsll((long long)mm) - 1;
+      if (k < kMaxD) s_zl[k] = lane * 32 + bit / 2;
+      ++k;
+      mm &= mm - 1;
+    }
+    if (lane == 31) s_zl[kMaxD] = x;
+  }
+  if (lane < D) {
+    const double xd = st.X[(long long)lane * Vcap + v];
+    const float h = static_cast<float>(xd);
+    ahi[lane] = h;
+    alo[lane] = static_cast<float>(xd - static_cast<double>(h));
+    for (int dd = 0; dd < D; ++dd) J[lane * D + dd] = (lane == dd) ? 1.f : 0.f;
+  }
+  __syncwarp();
+  const int nz = s_zl[kMaxD];
+  const int nzc = nz < D ? nz : D;
+  int l_last = -1;  // highest layer among the zero-set neurons
+  for (int q = 0; q < nzc; ++q) {
+    const int h = s_zl[q] - m;
+    if (h < 0) continue;
+    int l = 0;
+    while (l + 1 < net.L && h >= net.off[l + 1]) ++l;
+    if (l > l_last) l_last = l;
+  }
+  int in = D;
+  for (int k = 0; k <= l_last; ++k) {
+    const int H = net.w[k + 1];
+    const float2* Wt = P + net.wofs[k];  // [in][H]: lanes read consecutive neurons
+    for (int r = lane; r < H; r += 32) {
+      const int entry = m + net.off[k] + r;
+      int zpos = -1;
+      for (int q = 0; q < nzc; ++q)
+        if (s_zl[q] == entry) zpos = q;
+      if (!(k < l_last || zpos >= 0)) continue;
+      const float2 bj = P[net.bofs[k] + r];
+      float sum = bj.x, err = bj.y;
+      float jd[kMaxD];
+#pragma unroll
+      for (int dd = 0; dd < kMaxD; ++dd) jd[dd] = 0.f;
+      for (int c = 0; c < in; ++c) {
+        const float2 w = Wt[(long long)c * H + r];
+        const float xh = w.x, xl = w.y, yh = ahi[c], yl = alo[c];
+        const float p = xh * yh;
+        float e = fmaf(xh, yh, -p);  // exact low part of the product
+        e = fmaf(xh, yl, e);         // cross terms of the low parts
+        e = fmaf(xl, yh, e);
+        const float t = sum + p;     // TwoSum(sum, p): t + its error is exact
+        const float bb = t - sum;
+        err += ((sum - (t - bb)) + (p - bb)) + e;
+        sum = t;
+#pragma unroll
+        for (int dd = 0; dd < kMaxD; ++dd)
+          if (dd < D) jd[dd] = fmaf(xh, J[c * D + dd], jd[dd]);
+      }
+      const ff z = ff_fast_two_sum(sum, err);
+      if (zpos >= 0) {
+        gv[zpos] = static_cast<double>(z.hi) + static_cast<double>(z.lo);
+        for (int dd = 0; dd < D; ++dd) A[zpos * D + dd] = jd[dd];
+      }
+      if (k < l_last) {
+        const bool act = ((sig[entry >> 5] >> (2 * (entry & 31))) & 3ull) == kPlus;
+        nhi[r] = act ? z.hi : 0.f;
+        nlo[r] = act ? z.lo : 0.f;
+        for (int dd = 0; dd < D; ++dd) Jn[r * D + dd] = act ? jd[dd] : 0.f;
+      }
+    }
+    __syncwarp();
+    float* t0 = ahi; ahi = nhi; nhi = t0;
+    float* t1 = alo; alo = nlo; nlo = t1;
+    float* t2 = J; J = Jn; Jn = t2;
+    in = H;
+  }
+  if (lane == 0) {
+    NewtonOut o{};
+    o.nz = nz;
+    o.l_last = l_last;
+    newton_solve(net, st, v, s_zl, nz, A, gv, o);
+    *out = o;
+  }
+  __syncwarp();
 }
 
 __device__ __forceinline__ void newton_cta(const NetDesc& net, const State& st, long long v, int e_end,
