@@ -120,6 +120,17 @@ def precision_d4(seed: int = 0) -> tuple:
     return he_normal_mlp([4, 128, 128, 128, 1], seed=seed).rounded_to_fp32(), Box.cube(4)
 
 
+def precision_d4_subbox(half_width: float = 0.02, seed: int = 0) -> tuple:
+    """The D=4 precision network on the centred sub-box [-h, h]^4.
+
+    The full box holds far more cells than the oracle (or device memory) can
+    take: the first layer alone can have up to C(128, 4) ~ 1e7 interior
+    vertices.  h = 0.02 gives about 2e5 vertices and 8e5 edges.
+    """
+    net, _ = precision_d4(seed)
+    return net, Box(np.full(4, -half_width), np.full(4, half_width))
+
+
 def diff_d3(seed: int = 0) -> tuple:
     """D=3, box [-1,1]^3, MLP 3-32-32-32-1 He-normal, rounded to FP32."""
     return he_normal_mlp([3, 32, 32, 32, 1], seed=seed).rounded_to_fp32(), Box.cube(3)
