@@ -29,6 +29,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) per k_layer launch, mixed precision, from one ncu
+# capture of this command (profiles/k_layer_torus_d3.md); set to None when
+# the kernel changes until it is captured again.
+K_LAYER_DRAM_BYTES_PER_LAUNCH = 105_200_000
+
 METRIC = "vertices+edges/s at D=3 (torus 3-64x4-1, box [-1,1]^3)"
 UNIT = "(V+E)/s"
 
@@ -213,7 +218,11 @@ def run_ours(args, rank, world, local_rank):
     achieved = sum(layer_bytes) / (loop_avg.sum() / 1e3) / 1e9
     roofline = {"kernel": "k_layer (persistent neuron loop, one launch per layer)", "bound": "hbm",
                 "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": peak_kind, "traffic": None,
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "traffic": K_LAYER_DRAM_BYTES_PER_LAUNCH if args.precision == "mixed" else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the k_layer launches of one "
+                                  "steady-state extraction of this workload (profiles/k_layer_torus_d3.md), "
+                                  "averaged per launch",
                 "bytes_per_launch_avg": int(sum(layer_bytes) / len(layer_bytes)),
                 "launch_ms_avg": round(float(loop_avg.mean()), 4),
                 "share_of_step": round(float(loop_avg.sum() / statistics.mean(step_ms)), 3),

@@ -37,47 +37,53 @@ struct NewtonOut {
 
 // One Newton step on the D zero entries of vertex v: rows are the facets'
 // (+-e_d, value from the stored coordinate) and the neurons' (gradient A,
-// value gv); Gaussian elimination with partial pivoting in float64.
+// value gv); Gaussian elimination with partial pivoting in T.  The residuals
+// are formed in float64; the step is small (the stored coordinates are
+// FP32-accurate), so solving for it in float32 (the polish) loses only
+// ~1e-7 x cond of the step itself, far below the coordinate tolerance.
+template <typename T = double>
 __device__ inline void newton_solve(const NetDesc& net, const State& st, long long v, const int* s_zl, int nz,
                                     const double* A, const double* gv, NewtonOut& o) {
   const int D = net.D, m = net.m;
   o.ok = 0;
   if (nz != D) return;
-  double M[kMaxD][kMaxD + 1];
+  T M[kMaxD][kMaxD + 1];
   for (int q = 0; q < D; ++q) {
     const int j = s_zl[q];
     if (j < m) {
       const int d = j >> 1;
       const double xd = st.X[(long long)d * st.Vcap + v];
-      for (int dd = 0; dd < D; ++dd) M[q][dd] = 0.0;
-      M[q][d] = (j & 1) ? -1.0 : 1.0;
-      M[q][D] = -((j & 1) ? (net.hi[d] - xd) : (xd - net.lo[d]));
+      for (int dd = 0; dd < D; ++dd) M[q][dd] = T(0);
+      M[q][d] = (j & 1) ? T(-1) : T(1);
+      M[q][D] = static_cast<T>(-((j & 1) ? (net.hi[d] - xd) : (xd - net.lo[d])));
     } else {
-      for (int dd = 0; dd < D; ++dd) M[q][dd] = A[q * D + dd];
-      M[q][D] = -gv[q];
+      for (int dd = 0; dd < D; ++dd) M[q][dd] = static_cast<T>(A[q * D + dd]);
+      M[q][D] = static_cast<T>(-gv[q]);
     }
   }
   for (int c = 0; c < D; ++c) {
     int piv = c;
     for (int r = c + 1; r < D; ++r)
       if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
-    if (M[piv][c] == 0.0) return;
+    if (M[piv][c] == T(0)) return;
     if (piv != c)
       for (int k2 = 0; k2 <= D; ++k2) {
-        const double t = M[c][k2];
+        const T t = M[c][k2];
         M[c][k2] = M[piv][k2];
         M[piv][k2] = t;
       }
     for (int r = c + 1; r < D; ++r) {
-      const double f = M[r][c] / M[c][c];
+      const T f = M[r][c] / M[c][c];
       for (int k2 = c; k2 <= D; ++k2) M[r][k2] -= f * M[c][k2];
     }
   }
+  T dl[kMaxD];
   for (int r = D - 1; r >= 0; --r) {
-    double acc = M[r][D];
-    for (int k2 = r + 1; k2 < D; ++k2) acc -= M[r][k2] * o.dlt[k2];
-    o.dlt[r] = acc / M[r][r];
+    T acc = M[r][D];
+    for (int k2 = r + 1; k2 < D; ++k2) acc -= M[r][k2] * dl[k2];
+    dl[r] = acc / M[r][r];
   }
+  for (int r = 0; r < D; ++r) o.dlt[r] = static_cast<double>(dl[r]);
   o.ok = 1;
 }
 
@@ -358,7 +364,7 @@ __device__ void newton_ff_warp(const NetDesc& net, const State& st, const float2
     NewtonOut o{};
     o.nz = nz;
     o.l_last = l_last;
-    newton_solve(net, st, v, s_zl, nz, A, gv, o);
+    newton_solve<float>(net, st, v, s_zl, nz, A, gv, o);
     *out = o;
   }
   __syncwarp();
