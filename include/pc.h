@@ -112,6 +112,14 @@ typedef struct {
   int gemm;               /* pc_gemm: layer-start product of FP32 values */
   int pairing;            /* pc_pairing: how step 5 matches the two
                              occurrences of a splitting 2-face */
+  int canonical;          /* 1: return the result in canonical order:
+                             vertices sorted by their packed sign words (word
+                             0 most significant, unsigned), edges renumbered
+                             and sorted by (smaller, larger) endpoint, so that
+                             two extractions give identical arrays; the
+                             values and error estimates follow the vertices.
+                             Not with keep_tape (PC_ERR_INVALID at pc_create):
+                             the tape refers to creation order */
 } pc_options;
 
 /* Fills *opt with defaults (mixed precision, persistent execution,

@@ -857,6 +857,7 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   if (c->opt.strict && (degenerate || undecided))
     throw PcError(PC_ERR_DEGENERATE, "genericity violated: " + std::to_string(degenerate) + " exact zeros, " +
                                           std::to_string(undecided) + " FP64-undecidable signs");
+  if (c->opt.canonical) pc_canonicalize(c);
 }
 
 void StateBufs::release(pc_ctx* c) {
@@ -940,7 +941,7 @@ pc_status pc_create(pc_ctx** out, int device, const pc_options* opt) {
   pc_default_options(&c->opt);
   if (opt) c->opt = *opt;
   if (c->opt.precision < 0 || c->opt.precision > 2 || c->opt.exec < 0 || c->opt.exec > 1 || c->opt.gemm < 0 ||
-      c->opt.gemm > 2 || c->opt.pairing < 0 || c->opt.pairing > 1) {
+      c->opt.gemm > 2 || c->opt.pairing < 0 || c->opt.pairing > 1 || (c->opt.canonical && c->opt.keep_tape)) {
     delete c;
     return PC_ERR_INVALID;
   }

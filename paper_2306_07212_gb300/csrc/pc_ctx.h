@@ -17,6 +17,9 @@ void* ctx_alloc(pc_ctx* c, size_t bytes);
 void ctx_free(pc_ctx* c, void*& p);
 pc::State pc_make_state(pc_ctx* c);
 
+// canonical output order (pc_canon.cu)
+void pc_canonicalize(pc_ctx* c);
+
 // tcgen05 3xTF32 layer-start product (pc_gemm_tc.cu)
 bool pc_gemm_tc_eligible(const pc::NetDesc& net, int l);
 cudaError_t pc_gemm_tc_set_attributes();
