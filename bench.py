@@ -246,6 +246,31 @@ def run_ours(args, rank, world, local_rank):
                "step_ms_median": round(statistics.median(step_ms), 4)}
         if cpu:
             out["cpu_baseline"] = cpu
+        if world == 1:
+            # the other precision modes on the same workload, same timing rules
+            # (reported beside the configured mixed-precision path)
+            variants = {}
+            for prec in ("fp64", "mixed") if args.precision != "mixed" else ("fp64",):
+                if prec == args.precision:
+                    continue
+                with Extractor(device=local_rank, precision=prec, execution=args.execution) as vx:
+                    for _ in range(args.warmup):
+                        vx.extract(net, box, params=params_dev)
+                    vms = []
+                    for _ in range(args.steps):
+                        flush.zero_()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        vx.extract(net, box, params=params_dev)
+                        e1.record()
+                        e1.synchronize()
+                        vms.append(e0.elapsed_time(e1))
+                    vc = vx.counts()
+                    vunits = vc["nV"] + vc["nE"]
+                variants[prec] = {"value": round(vunits * len(vms) / (sum(vms) / 1e3), 1), "unit": UNIT,
+                                  "ms_per_step": round(sum(vms) / len(vms), 4), "steps": len(vms),
+                                  "n_vertices": vc["nV"], "n_edges": vc["nE"]}
+            out["variants"] = variants
         if args.serve_requests > 0 and world == 1:
             lim = 1 << 30
             serving = {
