@@ -132,6 +132,24 @@ def neuron_loop_bytes(net, stats, precision: str) -> list:
     return out
 
 
+# -- replicas: whole-job numbers --------------------------------------------
+
+def max_over_ranks(seconds: float, dist=None) -> float:
+    """The slowest rank's time (the job ends when the last replica does)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return seconds
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step: int, steps: int, world: int, seconds: float) -> float:
+    """Units all replicas processed (each the same workload) per second of the slowest."""
+    return units_per_step * steps * world / seconds
+
+
 # -- our arm -------------------------------------------------------------------
 
 def run_ours(args, rank, world, local_rank):
@@ -181,10 +199,7 @@ def run_ours(args, rank, world, local_rank):
     launches = ex.diagnostics()["launches"] - launches0
     assert ex.counts()["nV"] + ex.counts()["nE"] == units
     total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(total_s, dist)
 
     # end to end through the C ABI with host buffers: parameters from pinned
     # host memory each step, the complex copied back to pinned host memory
@@ -205,10 +220,7 @@ def run_ours(args, rank, world, local_rank):
         ex._check(lib.pc_signvectors(ctx, None, None, Sh.data_ptr()))
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     h2d = params_host.numel() * 8
     d2h = Xh.numel() * 8 + Eh.numel() * 4 + Sh.numel() * 8
 
@@ -230,7 +242,7 @@ def run_ours(args, rank, world, local_rank):
     out = None
     if rank == 0:
         cpu = cpu_baseline(net, box) if world == 1 else None
-        value = units * args.steps * world / total_s
+        value = whole_job_rate(units, args.steps, world, total_s)
         out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": round(total_s * 1e3 / args.steps, 4), "higher_is_better": True,
@@ -240,7 +252,7 @@ def run_ours(args, rank, world, local_rank):
                "config": dict(config, precision=args.precision, execution=args.execution, n_vertices=c["nV"],
                               n_edges=c["nE"], l2="flushed by a 512 MiB write before every step",
                               parallelism="replicas" if world > 1 else "single GPU"),
-               "e2e": {"value": round(units * args.steps * world / e2e_s, 1), "unit": UNIT,
+               "e2e": {"value": round(whole_job_rate(units, args.steps, world, e2e_s), 1), "unit": UNIT,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": int(launches), "roofline": roofline, "clocks": clk,
                "step_ms_median": round(statistics.median(step_ms), 4)}
