@@ -103,7 +103,8 @@ typedef struct {
   int64_t mem_budget_bytes; /* 0 = no limit */
   double filter_kappa;    /* PC_PREC_MIXED: re-evaluate a sign in FP64 when
                              |z| <= kappa * (rms FP32 error estimate of z) */
-  int polish;             /* FP64 Newton polish of every vertex whose rms
+  int polish;             /* Newton polish (values in float-float arithmetic,
+                             about 44 bits) of every vertex whose rms
                              coordinate error estimate exceeds polish_tol *
                              box diameter: 1 on, 0 off, -1 on in
                              PC_PREC_MIXED only */
