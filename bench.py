@@ -10,7 +10,13 @@ CUDA events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle (the reference arm of this build)
+The JSON line also carries the FP64 mode on the same workload
+(`variants.fp64`), the serving measurement (`serving`: a Poisson stream of
+2000 extraction requests through the batched 8-slot server and the plain
+1-slot path; `--serve-requests 0` skips it), the roofline of the neuron loop,
+the clocks seen during the timed region and one oracle run on a host core.
+
+--impl reference times the FP64 CPU oracle as the reference arm
 on the host cores.  Under torchrun (N > 1) every rank runs an independent
 replica on its own GPU (the extraction does not shard); rank 0 prints one JSON
 line with the whole-job throughput.
