@@ -1,6 +1,8 @@
-// libpc core: device state management, the layer-start forward product
-// (step (1) of Section 4.2), the per-neuron phase kernels in both execution
-// modes, and the C ABI declared in include/pc.h.
+// libpc core: device state management, the set-up kernels, the SIMT
+// layer-start product (step (1) of Section 4.2; the tensor-core form is in
+// pc_gemm_tc.cu), the per-neuron phase kernels in both execution modes, the
+// exact check of fingerprint pairings, the coordinate polish, and the C ABI
+// declared in include/pc.h.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -20,7 +20,7 @@ pc::State pc_make_state(pc_ctx* c);
 // canonical output order (pc_canon.cu)
 void pc_canonicalize(pc_ctx* c);
 
-// tcgen05 3xTF32 layer-start product (pc_gemm_tc.cu)
+// tcgen05 layer-start product (pc_gemm_tc.cu)
 bool pc_gemm_tc_eligible(const pc::NetDesc& net, int l);
 cudaError_t pc_gemm_tc_set_attributes();
 cudaError_t pc_gemm_tc_launch(const pc::NetDesc& net, const pc::State& st, int l, long long vcap_tiles, int num_sms,

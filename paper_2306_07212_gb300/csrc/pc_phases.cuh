@@ -18,8 +18,12 @@
 //   phase_split  steps (4)+(5).  One warp per splitting edge interpolates the
 //       new vertex (FP64 t and coordinates, values in the value type), splits
 //       the edge into E+ and E-, and inserts the edge's parent 2-face keys
-//       into an open-addressing hash table.  The second arrival of a 2-face
-//       verifies the match exactly and emits the intersecting edge.
+//       into an open-addressing hash table.  Default: each slot holds the
+//       face's 64-bit fingerprint and the first occurrence's payload, written
+//       with one 128-bit CAS; the second occurrence pairs in the same atomic
+//       and records the pairing, which k_verify_pairs checks exactly after
+//       the last step.  Inline mode: the second occurrence compares the full
+//       face before it pairs.
 #pragma once
 
 #include "pc_device.cuh"
