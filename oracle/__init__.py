@@ -6,7 +6,10 @@ its Python binding) never does.  The C++ source in ``oracle.cpp`` is written
 from the paper and shares no code with the CUDA path.
 
 Functions
-  extract(net, box, max_neurons=-1)  edge subdivision (Section 4.2)
+  extract(net, box, max_neurons=-1, prune=False)
+                                     edge subdivision (Section 4.2); with
+                                     prune, the pruning during subdivision of
+                                     Section 5.4.2 (level-set extraction)
   brute(net, box, tol)               the complex from its definition
   faces(result)                      k-cell counts by perturbation (Section 4.1)
   grad(net, result, gx)              implicit-function gradient of a vertex loss
@@ -47,7 +50,8 @@ def _load():
             vp, i32p, f64p, i64p = (ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64))
             lib.orc_extract.restype = vp
-            lib.orc_extract.argtypes = [ctypes.c_int, i32p, f64p, f64p, f64p, ctypes.c_int]
+            lib.orc_extract.argtypes = [ctypes.c_int, i32p, f64p, f64p, f64p, ctypes.c_int, ctypes.c_int]
+            lib.orc_layer_counts.argtypes = [vp, i64p]
             lib.orc_brute.restype = vp
             lib.orc_brute.argtypes = [ctypes.c_int, i32p, f64p, f64p, f64p, ctypes.c_double]
             lib.orc_free.argtypes = [vp]
@@ -133,13 +137,21 @@ class _Handle:
             pass
 
 
-def extract(net, box, max_neurons: int = -1) -> Result:
+def extract(net, box, max_neurons: int = -1, prune: bool = False) -> Result:
     lib = _load()
     widths, params, lo, hi = _net_args(net, box)
     h = lib.orc_extract(net.L, _ptr(widths, ctypes.c_int32), _ptr(params, ctypes.c_double),
-                        _ptr(lo, ctypes.c_double), _ptr(hi, ctypes.c_double), int(max_neurons))
+                        _ptr(lo, ctypes.c_double), _ptr(hi, ctypes.c_double), int(max_neurons), int(prune))
     X, S, E, stats = _collect(lib, h, net.D)
     return Result(X, S, E, stats, lib.orc_status(h), lib.orc_error(h).decode(), net.D, _Handle(lib, h))
+
+
+def layer_counts(res: Result) -> np.ndarray:
+    """(layers, 2) vertices and edges after each completed layer (and its pruning)."""
+    lib = _load()
+    out = np.zeros((64, 2), np.int64)
+    n = lib.orc_layer_counts(res._handle.h, _ptr(out, ctypes.c_int64))
+    return out[:n]
 
 
 def brute(net, box, tol: float = 1e-9) -> Result:

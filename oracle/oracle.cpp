@@ -18,6 +18,11 @@
 //                 activation pattern, plus edges by a midpoint test.
 //   orc_grad      gradient of a vertex-position loss through the
 //                 implicit-function theorem on each vertex's D zero functions.
+//   pruning       (orc_extract with prune = 1) the pruning during edge
+//                 subdivision of Section 5.4.2 for level-set extraction: after
+//                 each layer but the last, edges whose two vertices have the
+//                 same signs w.r.t. all future neurons are dropped, and so are
+//                 the vertices left without an edge.
 //
 // Readings taken where the paper is silent (same rule on the GPU side):
 //   * W[l] is out x in and z = W x + b (the network form of Eq. 4, not the
@@ -80,6 +85,7 @@ struct Result {
   std::vector<int8_t> S;                // nV * P
   std::vector<std::array<int32_t, 2>> E;
   std::vector<int64_t> stats;           // per neuron: nsplit, nkeys, npairs, ndegenerate
+  std::vector<int64_t> layer_counts;    // per layer: vertices, edges after it (and its pruning)
   int status = 0;                       // 0 ok, 4 degenerate, 5 pairing
   std::string err;
   int64_t nV() const { return int64_t(X.size()) / D; }
@@ -111,9 +117,74 @@ void layer_preact(const Net& net, int m, int l, const double* x, const int8_t* s
   }
 }
 
+// Signs of the neurons of layers > l at x: layers <= l use the stored
+// activation pattern s (active iff +), later layers the real ReLU of the
+// values computed here.  Returns false if a future value is exactly 0.
+bool future_signs(const Net& net, int m, int l, const double* x, const int8_t* s, std::vector<int8_t>& fs) {
+  std::vector<double> a(x, x + net.w[0]), z;
+  fs.clear();
+  bool generic = true;
+  for (int k = 0; k < net.L; ++k) {
+    const int o = net.w[k + 1], in = net.w[k];
+    z.assign(o, 0.0);
+    for (int r = 0; r < o; ++r) {
+      double acc = net.b[k][r];
+      for (int c = 0; c < in; ++c) acc += net.W[k][size_t(r) * in + c] * a[c];
+      z[r] = acc;
+    }
+    a.assign(o, 0.0);
+    for (int r = 0; r < o; ++r) {
+      if (k <= l) {
+        a[r] = (s[m + net.off[k] + r] == 1) ? z[r] : 0.0;
+      } else {
+        if (z[r] == 0.0) generic = false;
+        fs.push_back(z[r] > 0.0 ? 1 : (z[r] < 0.0 ? -1 : 0));
+        a[r] = z[r] > 0.0 ? z[r] : 0.0;
+      }
+    }
+  }
+  return generic;
+}
+
+// Pruning during edge subdivision (Section 5.4.2), after layer l: an edge
+// whose vertices have the same signs w.r.t. every future neuron is crossed by
+// no future folded hyperplane (along the edge each next layer is affine, and
+// by induction so are the later ones once no earlier neuron splits it), so it
+// cannot meet the zero set of the output; it is dropped, and so is every
+// vertex left without an edge.  An exactly zero future value keeps its edges.
+void prune_after_layer(const Net& net, int l, Result& R) {
+  const int D = R.D, m = R.m, P = R.P;
+  const int64_t nV = R.nV();
+  std::vector<std::vector<int8_t>> fs(nV);
+  std::vector<char> generic(nV);
+  for (int64_t v = 0; v < nV; ++v)
+    generic[v] = future_signs(net, m, l, &R.X[size_t(v) * D], &R.S[size_t(v) * P], fs[v]);
+  std::vector<std::array<int32_t, 2>> kept;
+  std::vector<char> used(nV, 0);
+  for (const auto& e : R.E) {
+    if (generic[e[0]] && generic[e[1]] && fs[e[0]] == fs[e[1]]) continue;
+    kept.push_back(e);
+    used[e[0]] = used[e[1]] = 1;
+  }
+  std::vector<int32_t> idx(nV, -1);
+  std::vector<double> X;
+  std::vector<int8_t> S;
+  int32_t k = 0;
+  for (int64_t v = 0; v < nV; ++v) {
+    if (!used[v]) continue;
+    idx[v] = k++;
+    X.insert(X.end(), R.X.begin() + size_t(v) * D, R.X.begin() + size_t(v + 1) * D);
+    S.insert(S.end(), R.S.begin() + size_t(v) * P, R.S.begin() + size_t(v + 1) * P);
+  }
+  for (auto& e : kept) e = {idx[e[0]], idx[e[1]]};
+  R.X.swap(X);
+  R.S.swap(S);
+  R.E.swap(kept);
+}
+
 // Edge subdivision (Section 4.2), all neurons in index order (or the first
 // `max_neurons` of them when max_neurons >= 0).
-void extract(const Net& net, const double* lo, const double* hi, int max_neurons, Result& R) {
+void extract(const Net& net, const double* lo, const double* hi, int max_neurons, Result& R, bool prune) {
   const int D = net.w[0], m = 2 * D, N = net.N, P = m + N;
   R.D = D; R.m = m; R.N = N; R.P = P;
   R.stats.assign(size_t(N) * 4, 0);
@@ -221,6 +292,9 @@ void extract(const Net& net, const double* lo, const double* hi, int max_neurons
         R.err = "exact zero pre-activation (non-generic arrangement)";
       }
     }
+    if (prune && l + 1 < net.L) prune_after_layer(net, l, R);
+    R.layer_counts.push_back(R.nV());
+    R.layer_counts.push_back(int64_t(R.E.size()));
   }
 }
 
@@ -543,11 +617,18 @@ int grad(const Net& net, const Result& R, const double* gx, double* dtheta) {
 extern "C" {
 
 void* orc_extract(int L, const int32_t* widths, const double* params, const double* lo,
-                  const double* hi, int max_neurons) {
+                  const double* hi, int max_neurons, int prune) {
   Result* R = new Result;
   const Net net = make_net(L, widths, params);
-  extract(net, lo, hi, max_neurons, *R);
+  extract(net, lo, hi, max_neurons, *R, prune != 0);
   return R;
+}
+
+// (vertices, edges) after each completed layer: 2 int64 per layer.
+int orc_layer_counts(void* r, int64_t* out) {
+  auto* R = static_cast<Result*>(r);
+  std::memcpy(out, R->layer_counts.data(), R->layer_counts.size() * sizeof(int64_t));
+  return int(R->layer_counts.size() / 2);
 }
 
 void* orc_brute(int L, const int32_t* widths, const double* params, const double* lo,
