@@ -121,6 +121,14 @@ typedef struct {
                              values and error estimates follow the vertices.
                              Not with keep_tape (PC_ERR_INVALID at pc_create):
                              the tape refers to creation order */
+  int prune;              /* 1: pruning during edge subdivision (Section
+                             5.4.2) for level-set extraction: after each layer
+                             but the last, edges whose vertices have the same
+                             signs w.r.t. all future neurons (FP64 forward
+                             pass at the vertex) are dropped, and at the end
+                             the vertices without an edge; the result keeps
+                             the output neuron's zero set and its
+                             neighbourhood.  Not with keep_tape */
 } pc_options;
 
 /* Fills *opt with defaults (mixed precision, persistent execution,

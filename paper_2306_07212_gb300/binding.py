@@ -57,7 +57,8 @@ class Options(ctypes.Structure):
                 ("strict", ctypes.c_int), ("init_vcap", ctypes.c_int64), ("init_ecap", ctypes.c_int64),
                 ("mem_budget_bytes", ctypes.c_int64), ("filter_kappa", ctypes.c_double),
                 ("polish", ctypes.c_int), ("polish_tol", ctypes.c_double), ("timers", ctypes.c_int),
-                ("gemm", ctypes.c_int), ("pairing", ctypes.c_int), ("canonical", ctypes.c_int)]
+                ("gemm", ctypes.c_int), ("pairing", ctypes.c_int), ("canonical", ctypes.c_int),
+                ("prune", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -150,7 +151,7 @@ class Extractor:
                  keep_tape: bool = False, strict: bool = False, init_vcap: int = 0, init_ecap: int = 0,
                  mem_budget_bytes: int = 0, kappa: float = 12.0, polish: int = -1, polish_tol: float = 1e-6,
                  timers: bool = False, torch_allocator: bool = True, gemm: str = "tensor",
-                 pairing: str = "deferred", canonical: bool = False):
+                 pairing: str = "deferred", canonical: bool = False, prune: bool = False):
         self._lib = load_library()
         o = Options()
         self._lib.pc_default_options(ctypes.byref(o))
@@ -167,6 +168,7 @@ class Extractor:
         o.gemm = GEMM[gemm]
         o.pairing = PAIRING[pairing]
         o.canonical = int(canonical)
+        o.prune = int(prune)
         self.device = device
         self.options = o
         self._ctx = ctypes.c_void_p()

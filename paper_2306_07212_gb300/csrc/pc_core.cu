@@ -613,6 +613,7 @@ static void enqueue(pc_ctx* c, int l0, int i0, bool gemm_done) {
   for (int l = l0; l < c->net.L; ++l) {
     if (!(l == l0 && gemm_done)) Kernels<ZT, MIXED>::gemm(c, st, l);
     Kernels<ZT, MIXED>::layer(c, st, l, l == l0 ? i0 : 0);
+    if (c->opt.prune && l + 1 < c->net.L) pc_prune_edges(c, st, l);
   }
 }
 
@@ -859,6 +860,7 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   if (c->opt.strict && (degenerate || undecided))
     throw PcError(PC_ERR_DEGENERATE, "genericity violated: " + std::to_string(degenerate) + " exact zeros, " +
                                           std::to_string(undecided) + " FP64-undecidable signs");
+  if (c->opt.prune) pc_prune_vertices(c);
   if (c->opt.canonical) pc_canonicalize(c);
 }
 
@@ -943,7 +945,8 @@ pc_status pc_create(pc_ctx** out, int device, const pc_options* opt) {
   pc_default_options(&c->opt);
   if (opt) c->opt = *opt;
   if (c->opt.precision < 0 || c->opt.precision > 2 || c->opt.exec < 0 || c->opt.exec > 1 || c->opt.gemm < 0 ||
-      c->opt.gemm > 2 || c->opt.pairing < 0 || c->opt.pairing > 1 || (c->opt.canonical && c->opt.keep_tape)) {
+      c->opt.gemm > 2 || c->opt.pairing < 0 || c->opt.pairing > 1 || (c->opt.canonical && c->opt.keep_tape) ||
+      (c->opt.prune && c->opt.keep_tape)) {
     delete c;
     return PC_ERR_INVALID;
   }

@@ -20,6 +20,10 @@ pc::State pc_make_state(pc_ctx* c);
 // canonical output order (pc_canon.cu)
 void pc_canonicalize(pc_ctx* c);
 
+// pruning during subdivision (pc_prune.cu)
+void pc_prune_edges(pc_ctx* c, const pc::State& st, int l);
+void pc_prune_vertices(pc_ctx* c);
+
 // tcgen05 layer-start product (pc_gemm_tc.cu)
 bool pc_gemm_tc_eligible(const pc::NetDesc& net, int l);
 cudaError_t pc_gemm_tc_set_attributes();

@@ -76,7 +76,8 @@ struct Counters {        // 128 bytes
   long long nsplit, nkeys, npairs;
   long long nfilter, nundecided, ndegenerate;
   long long tsize;
-  long long pad[7];
+  long long pruned_e1;   // 0, or 1 + the edge count left by pruning after this step
+  long long pad[6];
 };
 
 struct Global {

@@ -205,7 +205,7 @@ __device__ void phase_classify(const NetDesc& net, const State& st, int zb, int 
                                Smem& sm, double* ws, int mw) {
   const Counters* prev = st.cnt + n;
   const long long nV = prev->nV_before + prev->nsplit;
-  const long long nE = prev->nE_before + prev->nsplit + prev->npairs;
+  const long long nE = prev->pruned_e1 > 0 ? prev->pruned_e1 - 1 : prev->nE_before + prev->nsplit + prev->npairs;
   Counters* cur = st.cnt + n + 1;
   if (nV < 0 || nV > st.Vcap || nE < 0 || nE > st.Ecap) {
     if (threadIdx.x == 0) report_corrupt(st.g, 2, n, nV, nE, st.Vcap);
