@@ -202,6 +202,16 @@ pc_status pc_stats(pc_ctx *ctx, int64_t *out, int n_neurons);
  * overwritten.  Needs keep_tape = 1 at extraction (else PC_ERR_NO_TAPE). */
 pc_status pc_backward(pc_ctx *ctx, const double *grad_x, double *grad_params, void *stream);
 
+/* k-cell counts of the last extraction's complex (Section 4.1: the k-faces
+ * by perturbing the zeros of the (k-1)-faces, a box facet's zero only toward
+ * the inside): f_out[k] for k = 0..D (f_out needs n >= D + 1 entries;
+ * f_out[D] is the number of regions), and optionally the Euler
+ * characteristic sum (-1)^k f_k (1 for the subdivided box).  Runs on the
+ * device; deduplicates the cells of each level by 64-bit fingerprints with
+ * an exact check of every duplicate (PC_ERR_PAIRING on a collision,
+ * PC_ERR_DEGENERATE on a non-generic cell).  Blocks until done. */
+pc_status pc_cell_counts(pc_ctx *ctx, int64_t *f_out, int n, int64_t *euler);
+
 /* Diagnostics of the last extraction, up to n int64 values: kernel launches
  * (cumulative over the context's life), capacity growths, polished vertices,
  * exact-zero pre-activations, FP64-undecidable signs, vertex / edge / hash

@@ -31,7 +31,7 @@ EXPORTS = ["pc_default_options", "pc_create", "pc_destroy", "pc_set_allocator", 
            "pc_diagnostics", "pc_kernel_times", "pc_error_estimates", "pc_values", "pc_extract_noalloc",
            "pc_estimate_bytes", "pc_server_default_options", "pc_server_create", "pc_server_submit",
            "pc_server_poll", "pc_server_error", "pc_server_wait_all", "pc_server_outputs", "pc_server_release", "pc_server_stats",
-           "pc_server_destroy", "pc_last_error"]
+           "pc_server_destroy", "pc_last_error", "pc_cell_counts"]
 
 
 class PcError(RuntimeError):
@@ -111,6 +111,7 @@ def load_library(path: str = LIB):
         lib.pc_extract_noalloc.argtypes = [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, vp, vp, vp,
                                            ctypes.c_int64, ctypes.c_int64, i64p, i64p, vp]
         lib.pc_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+        lib.pc_cell_counts.argtypes = [vp, i64p, ctypes.c_int, i64p]
         lib.pc_last_error.argtypes = [vp]
         lib.pc_last_error.restype = ctypes.c_char_p
         for f in EXPORTS:
@@ -312,6 +313,15 @@ class Extractor:
             self._check(f(self._ctx, ctypes.byref(p), ctypes.byref(ld), None))
             res.append((p.value, ld.value))
         return res
+
+    def cell_counts(self):
+        """(f_0, ..., f_D) k-cell counts of the last result and the Euler characteristic."""
+        D = self.counts()["D"]
+        f = np.zeros(D + 1, np.int64)
+        chi = ctypes.c_int64()
+        self._check(self._lib.pc_cell_counts(self._ctx, f.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), D + 1,
+                                             ctypes.byref(chi)))
+        return f, int(chi.value)
 
     def vertices_into(self, out) -> None:
         """Copies the D x nV coordinate block into `out` (host or device memory)."""
