@@ -53,3 +53,27 @@ def test_default_options_without_gpu(lib_path):
     o = binding.Options()
     lib.pc_default_options(ctypes.byref(o))
     assert o.precision == 1 and o.exec == 0 and o.filter_kappa == 12.0 and o.polish == -1 and o.gemm == 0
+
+
+def test_memory_estimate_covers_the_oracle_complex(lib_path):
+    """The serving admission estimate (pc_estimate_bytes, host-only) covers
+    the device bytes of the complex the oracle extracts for random nets of the
+    serving mix (coordinates, two value rows per vertex, sign words, edges,
+    staging), with room for one capacity doubling."""
+    import numpy as np
+    import oracle
+    from paper_2306_07212_gb300 import workloads as wl
+    from paper_2306_07212_gb300.binding import estimate_bytes
+    for D, depth, width, seed in [(2, 2, 16, 0), (2, 4, 32, 1), (3, 2, 16, 2), (3, 3, 16, 3), (4, 2, 8, 4),
+                                  (2, 6, 16, 5), (3, 2, 32, 6)]:
+        net = wl.he_normal_mlp([D] + [width] * depth + [1], seed=seed)
+        r = oracle.extract(net, wl.Box.cube(D))
+        S = (2 * D + net.n_neurons + 31) // 32
+        need = r.nV * (8 * D + 2 * 4 * width + 8 + 8 * S) + len(r.E) * (8 + 16)
+        est = estimate_bytes(net)
+        assert est >= 2 * need, (D, depth, width, est, need)
+        assert est < 1e12
+    # monotone in width and depth
+    small = estimate_bytes(wl.he_normal_mlp([3, 16, 16, 1], seed=0))
+    assert estimate_bytes(wl.he_normal_mlp([3, 32, 16, 1], seed=0)) > small
+    assert estimate_bytes(wl.he_normal_mlp([3, 16, 16, 16, 1], seed=0)) > small
