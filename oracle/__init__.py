@@ -11,6 +11,9 @@ Functions
                                      prune, the pruning during subdivision of
                                      Section 5.4.2 (level-set extraction)
   brute(net, box, tol)               the complex from its definition
+  extract_domain(net, dom), brute_domain(net, dom)
+                                     the same on a polyhedral domain of
+                                     half-spaces (e.g. a simplex)
   faces(result)                      k-cell counts by perturbation (Section 4.1)
   grad(net, result, gx)              implicit-function gradient of a vertex loss
 """
@@ -52,6 +55,11 @@ def _load():
             lib.orc_extract.restype = vp
             lib.orc_extract.argtypes = [ctypes.c_int, i32p, f64p, f64p, f64p, ctypes.c_int, ctypes.c_int]
             lib.orc_layer_counts.argtypes = [vp, i64p]
+            lib.orc_extract_domain.restype = vp
+            lib.orc_extract_domain.argtypes = [ctypes.c_int, i32p, f64p, ctypes.c_int, f64p, f64p, ctypes.c_int64,
+                                               f64p, ctypes.c_int64, i32p, ctypes.c_int, ctypes.c_int]
+            lib.orc_brute_domain.restype = vp
+            lib.orc_brute_domain.argtypes = [ctypes.c_int, i32p, f64p, ctypes.c_int, f64p, f64p, ctypes.c_double]
             lib.orc_brute.restype = vp
             lib.orc_brute.argtypes = [ctypes.c_int, i32p, f64p, f64p, f64p, ctypes.c_double]
             lib.orc_free.argtypes = [vp]
@@ -101,7 +109,7 @@ class Result:
         return self.E.shape[0]
 
 
-def _collect(lib, h, D, with_stats=True):
+def _collect(lib, h, D, with_stats=True, m=None):
     nV, nE, P = lib.orc_nv(h), lib.orc_ne(h), lib.orc_nsig(h)
     X = np.empty((nV, D), np.float64)
     S = np.empty((nV, P), np.int8)
@@ -111,7 +119,7 @@ def _collect(lib, h, D, with_stats=True):
         lib.orc_signs(h, _ptr(S, ctypes.c_int8))
     if nE:
         lib.orc_edges(h, _ptr(E, ctypes.c_int32))
-    N = P - 2 * D
+    N = P - (2 * D if m is None else m)
     stats = np.zeros((N, 4), np.int64)
     if with_stats and N:
         lib.orc_stats(h, _ptr(stats, ctypes.c_int64))
@@ -144,6 +152,40 @@ def extract(net, box, max_neurons: int = -1, prune: bool = False) -> Result:
                         _ptr(lo, ctypes.c_double), _ptr(hi, ctypes.c_double), int(max_neurons), int(prune))
     X, S, E, stats = _collect(lib, h, net.D)
     return Result(X, S, E, stats, lib.orc_status(h), lib.orc_error(h).decode(), net.D, _Handle(lib, h))
+
+
+def _domain_args(dom):
+    A = np.ascontiguousarray(dom.A, np.float64)
+    c = np.ascontiguousarray(dom.c, np.float64)
+    X0 = np.ascontiguousarray(dom.X0, np.float64)
+    E0 = np.ascontiguousarray(dom.E0, np.int32)
+    return A, c, X0, E0
+
+
+def extract_domain(net, dom, max_neurons: int = -1, prune: bool = False) -> Result:
+    """Edge subdivision on a polyhedral domain (half-spaces dom.c - dom.A x >= 0,
+    initial skeleton dom.X0, dom.E0)."""
+    lib = _load()
+    widths, params, _, _ = _net_args(net, type("B", (), {"lo": np.zeros(1), "hi": np.zeros(1)}))
+    A, c, X0, E0 = _domain_args(dom)
+    h = lib.orc_extract_domain(net.L, _ptr(widths, ctypes.c_int32), _ptr(params, ctypes.c_double), len(c),
+                               _ptr(A, ctypes.c_double), _ptr(c, ctypes.c_double), len(X0),
+                               _ptr(X0, ctypes.c_double), len(E0), _ptr(E0, ctypes.c_int32), int(max_neurons),
+                               int(prune))
+    X, S, E, stats = _collect(lib, h, net.D, m=len(c))
+    return Result(X, S, E, stats, lib.orc_status(h), lib.orc_error(h).decode(), net.D, _Handle(lib, h))
+
+
+def brute_domain(net, dom, tol: float = 1e-9) -> Result:
+    """The complex from its definition on a polyhedral domain."""
+    lib = _load()
+    widths, params, _, _ = _net_args(net, type("B", (), {"lo": np.zeros(1), "hi": np.zeros(1)}))
+    A, c, _, _ = _domain_args(dom)
+    h = lib.orc_brute_domain(net.L, _ptr(widths, ctypes.c_int32), _ptr(params, ctypes.c_double), len(c),
+                             _ptr(A, ctypes.c_double), _ptr(c, ctypes.c_double), float(tol))
+    X, S, E, _ = _collect(lib, h, net.D, with_stats=False, m=len(c))
+    return Result(X, S, E, np.zeros((0, 4), np.int64), lib.orc_status(h), lib.orc_error(h).decode(), net.D,
+                  _Handle(lib, h))
 
 
 def layer_counts(res: Result) -> np.ndarray:

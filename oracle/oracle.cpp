@@ -18,6 +18,9 @@
 //                 activation pattern, plus edges by a midpoint test.
 //   orc_grad      gradient of a vertex-position loss through the
 //                 implicit-function theorem on each vertex's D zero functions.
+//   domains       (orc_extract_domain, orc_brute_domain) a bounded polyhedral
+//                 domain of m half-spaces c - A x >= 0 (Section 4.1) with
+//                 the caller's initial 1-skeleton, e.g. a simplex.
 //   pruning       (orc_extract with prune = 1) the pruning during edge
 //                 subdivision of Section 5.4.2 for level-set extraction: after
 //                 each layer but the last, edges whose two vertices have the
@@ -182,8 +185,10 @@ void prune_after_layer(const Net& net, int l, Result& R) {
   R.E.swap(kept);
 }
 
-// Edge subdivision (Section 4.2), all neurons in index order (or the first
-// `max_neurons` of them when max_neurons >= 0).
+void subdivide(const Net& net, int max_neurons, Result& R, bool prune);
+
+// Edge subdivision (Section 4.2) on the box [lo, hi]^D, all neurons in index
+// order (or the first `max_neurons` of them when max_neurons >= 0).
 void extract(const Net& net, const double* lo, const double* hi, int max_neurons, Result& R, bool prune) {
   const int D = net.w[0], m = 2 * D, N = net.N, P = m + N;
   R.D = D; R.m = m; R.N = N; R.P = P;
@@ -204,7 +209,61 @@ void extract(const Net& net, const double* lo, const double* hi, int max_neurons
   for (int d = 0; d < D; ++d)
     for (int c = 0; c < nc; ++c)
       if (!((c >> d) & 1)) R.E.push_back({int32_t(c), int32_t(c | (1 << d))});
+  subdivide(net, max_neurons, R, prune);
+}
 
+// A bounded polyhedral domain given by m affine half-spaces (Section 4.1):
+// facet i is c_i - a_i . x >= 0 (sign entry i, + inside).
+struct Domain {
+  int m = 0;
+  std::vector<double> A;  // m x D, row-major
+  std::vector<double> c;  // m
+  double value(int i, int D, const double* x) const {
+    double v = c[i];
+    for (int d = 0; d < D; ++d) v -= A[size_t(i) * D + d] * x[d];
+    return v;
+  }
+  double scale(int i, int D, const double* x) const {
+    double s = std::fabs(c[i]);
+    for (int d = 0; d < D; ++d) s += std::fabs(A[size_t(i) * D + d] * x[d]);
+    return s;
+  }
+};
+
+// Edge subdivision on a polyhedral domain whose 1-skeleton (nv0 vertices X0,
+// ne0 edges E0) the caller gives: the facet entries of each initial vertex are
+// 0 on the facet (|value| <= 1e-12 of its scale) and + inside.  The facets'
+// zeros are perturbed only toward + in step (5), as for the box.
+void extract_domain(const Net& net, const Domain& dom, int64_t nv0, const double* X0, int64_t ne0,
+                    const int32_t* E0, int max_neurons, Result& R, bool prune) {
+  const int D = net.w[0], m = dom.m, N = net.N, P = m + N;
+  R.D = D; R.m = m; R.N = N; R.P = P;
+  R.stats.assign(size_t(N) * 4, 0);
+  for (int64_t v = 0; v < nv0; ++v) {
+    const double* x = X0 + size_t(v) * D;
+    R.X.insert(R.X.end(), x, x + D);
+    std::vector<int8_t> s(P, 0);
+    for (int i = 0; i < m; ++i) {
+      const double f = dom.value(i, D, x);
+      if (std::fabs(f) <= 1e-12 * dom.scale(i, D, x)) {
+        s[i] = 0;
+      } else if (f > 0) {
+        s[i] = 1;
+      } else {
+        R.status = 1;
+        R.err = "an initial vertex lies outside the domain";
+        s[i] = 1;
+      }
+    }
+    R.S.insert(R.S.end(), s.begin(), s.end());
+  }
+  for (int64_t e = 0; e < ne0; ++e) R.E.push_back({E0[2 * e], E0[2 * e + 1]});
+  if (R.status == 0) subdivide(net, max_neurons, R, prune);
+}
+
+// The neuron steps of edge subdivision on the current R (Section 4.2).
+void subdivide(const Net& net, int max_neurons, Result& R, bool prune) {
+  const int D = R.D, m = R.m, P = R.P;
   std::vector<double> Z, zt;  // Z: nV * H values of the current layer
   for (int l = 0; l < net.L; ++l) {
     const int H = net.w[l + 1];
@@ -382,15 +441,34 @@ bool solve(int n, std::vector<double> A, std::vector<double> rhs, std::vector<do
 }
 
 // Value of entry j (facet or neuron) at x given all neuron values zall.
-inline double entry_value(int j, int D, const double* lo, const double* hi, const double* x,
-                          const std::vector<double>& zall) {
-  const int m = 2 * D;
-  if (j < m) return (j % 2 == 0) ? x[j / 2] - lo[j / 2] : hi[j / 2] - x[j / 2];
-  return zall[j - m];
+inline double entry_value(int j, int D, const Domain& dom, const double* x, const std::vector<double>& zall) {
+  if (j < dom.m) return dom.value(j, D, x);
+  return zall[j - dom.m];
 }
 
+// The box [lo, hi]^D as half-spaces: 2d: x_d - lo_d >= 0, 2d+1: hi_d - x_d >= 0.
+Domain box_domain(int D, const double* lo, const double* hi) {
+  Domain dom;
+  dom.m = 2 * D;
+  dom.A.assign(size_t(2 * D) * D, 0.0);
+  dom.c.assign(2 * D, 0.0);
+  for (int d = 0; d < D; ++d) {
+    dom.A[size_t(2 * d) * D + d] = -1.0;
+    dom.c[2 * d] = -lo[d];
+    dom.A[size_t(2 * d + 1) * D + d] = 1.0;
+    dom.c[2 * d + 1] = hi[d];
+  }
+  return dom;
+}
+
+int brute_domain(const Net& net, const Domain& dom, double tol, Result& R);
+
 int brute(const Net& net, const double* lo, const double* hi, double tol, Result& R) {
-  const int D = net.w[0], m = 2 * D, N = net.N, P = m + N;
+  return brute_domain(net, box_domain(net.w[0], lo, hi), tol, R);
+}
+
+int brute_domain(const Net& net, const Domain& dom, double tol, Result& R) {
+  const int D = net.w[0], m = dom.m, N = net.N, P = m + N;
   R.D = D; R.m = m; R.N = N; R.P = P;
   int Nh = 0;  // neurons whose state changes the affine map: all but the last layer
   for (int l = 0; l + 1 < net.L; ++l) Nh += net.w[l + 1];
@@ -399,14 +477,11 @@ int brute(const Net& net, const double* lo, const double* hi, double tol, Result
   std::vector<double> G(size_t(P) * D), c(P), zall, x;
   std::vector<int> idx(D);
   for (uint64_t pat = 0; pat < (uint64_t(1) << Nh); ++pat) {
-    // Affine map of every entry under activation pattern `pat`.
-    for (int d = 0; d < D; ++d) {
-      for (int k = 0; k < D; ++k) {
-        G[size_t(2 * d) * D + k] = (k == d) ? 1.0 : 0.0;
-        G[size_t(2 * d + 1) * D + k] = (k == d) ? -1.0 : 0.0;
-      }
-      c[2 * d] = -lo[d];
-      c[2 * d + 1] = hi[d];
+    // Affine map of every entry under activation pattern `pat`; facet i is
+    // (-a_i) . x + c_i.
+    for (int i = 0; i < m; ++i) {
+      for (int k = 0; k < D; ++k) G[size_t(i) * D + k] = -dom.A[size_t(i) * D + k];
+      c[i] = dom.c[i];
     }
     std::vector<double> aG(size_t(D) * D, 0.0), ac(D, 0.0);  // input: identity map
     for (int d = 0; d < D; ++d) aG[size_t(d) * D + d] = 1.0;
@@ -450,7 +525,7 @@ int brute(const Net& net, const double* lo, const double* hi, double tol, Result
         std::vector<int8_t> s(P, 0);
         int zi = 0;
         for (int j = 0; j < P && ok; ++j) {
-          const double val = entry_value(j, D, lo, hi, x.data(), zall);
+          const double val = entry_value(j, D, dom, x.data(), zall);
           const bool in_set = (zi < D && idx[zi] == j);
           if (in_set) {
             ++zi;
@@ -498,7 +573,7 @@ int brute(const Net& net, const double* lo, const double* hi, double tol, Result
       forward_all(net, mid.data(), zall);
       bool ok = true;
       for (int j = 0; j < P && ok; ++j) {
-        const double val = entry_value(j, D, lo, hi, mid.data(), zall);
+        const double val = entry_value(j, D, dom, mid.data(), zall);
         if (j8[j] == 0) ok = std::fabs(val) <= tol;
         else ok = (std::fabs(val) > tol) && ((val > 0) == (j8[j] > 0));
       }
@@ -621,6 +696,37 @@ void* orc_extract(int L, const int32_t* widths, const double* params, const doub
   Result* R = new Result;
   const Net net = make_net(L, widths, params);
   extract(net, lo, hi, max_neurons, *R, prune != 0);
+  return R;
+}
+
+// Edge subdivision on the polyhedral domain c - A x >= 0 (m half-spaces,
+// A row-major m x D) with the caller's initial 1-skeleton (nv0 vertices X0
+// row-major nv0 x D, ne0 edges E0 as pairs).
+void* orc_extract_domain(int L, const int32_t* widths, const double* params, int m, const double* A,
+                         const double* c, int64_t nv0, const double* X0, int64_t ne0, const int32_t* E0,
+                         int max_neurons, int prune) {
+  Result* R = new Result;
+  const Net net = make_net(L, widths, params);
+  Domain dom;
+  dom.m = m;
+  dom.A.assign(A, A + size_t(m) * widths[0]);
+  dom.c.assign(c, c + m);
+  extract_domain(net, dom, nv0, X0, ne0, E0, max_neurons, *R, prune != 0);
+  return R;
+}
+
+void* orc_brute_domain(int L, const int32_t* widths, const double* params, int m, const double* A,
+                       const double* c, double tol) {
+  Result* R = new Result;
+  const Net net = make_net(L, widths, params);
+  Domain dom;
+  dom.m = m;
+  dom.A.assign(A, A + size_t(m) * widths[0]);
+  dom.c.assign(c, c + m);
+  if (brute_domain(net, dom, tol, *R) != 0) {
+    R->status = 1;
+    R->err = "network too large for brute force";
+  }
   return R;
 }
 

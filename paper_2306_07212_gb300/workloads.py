@@ -115,6 +115,46 @@ def torus_d3() -> tuple:
     return Net(widths, W, b), Box.cube(3)
 
 
+@dataclasses.dataclass
+class Polytope:
+    """A bounded domain {x : c - A x >= 0} with its 1-skeleton (vertices X0,
+    edges E0 as index pairs)."""
+
+    A: np.ndarray
+    c: np.ndarray
+    X0: np.ndarray
+    E0: np.ndarray
+
+    @property
+    def D(self) -> int:
+        return self.A.shape[1]
+
+    @staticmethod
+    def simplex(D: int, lo: float = -1.0, size: float = 2.0) -> "Polytope":
+        """{x_d >= lo for all d, sum_d (x_d - lo) <= size}: D + 1 vertices
+        (the corner lo and lo + size e_d), every pair an edge."""
+        A = np.vstack([-np.eye(D), np.ones((1, D))])
+        c = np.concatenate([np.full(D, -lo), [size + D * lo]])
+        X0 = np.vstack([np.full(D, lo)] + [np.full(D, lo) + size * np.eye(D)[d] for d in range(D)])
+        E0 = np.array([(i, j) for i in range(D + 1) for j in range(i + 1, D + 1)], np.int32)
+        return Polytope(A, c, X0, E0)
+
+    @staticmethod
+    def from_box(box: "Box") -> "Polytope":
+        """The box as 2D half-spaces (2d: x_d - lo_d >= 0, 2d+1: hi_d - x_d >= 0)
+        with its corners (corner c has coordinate d at hi iff bit d of c is set)
+        and axis edges, in the order the box extraction uses."""
+        D = len(box.lo)
+        A = np.zeros((2 * D, D))
+        c = np.zeros(2 * D)
+        for d in range(D):
+            A[2 * d, d], c[2 * d] = -1.0, -box.lo[d]
+            A[2 * d + 1, d], c[2 * d + 1] = 1.0, box.hi[d]
+        X0 = np.array([[box.hi[d] if (k >> d) & 1 else box.lo[d] for d in range(D)] for k in range(1 << D)])
+        E0 = np.array([(k, k | (1 << d)) for d in range(D) for k in range(1 << D) if not (k >> d) & 1], np.int32)
+        return Polytope(A, c, X0, E0)
+
+
 def precision_d4(seed: int = 0) -> tuple:
     """D=4, box [-1,1]^4, MLP 4-128-128-128-1 He-normal, rounded once to FP32."""
     return he_normal_mlp([4, 128, 128, 128, 1], seed=seed).rounded_to_fp32(), Box.cube(4)
