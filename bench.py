@@ -10,8 +10,8 @@ CUDA events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-The JSON line also carries the FP64 mode on the same workload
-(`variants.fp64`), the serving measurement (`serving`: a Poisson stream of
+The JSON line also carries the FP64 mode and the pruned (level-set)
+extraction on the same workload (`variants`), the serving measurement (`serving`: a Poisson stream of
 2000 extraction requests through the batched 8-slot server and the plain
 1-slot path; `--serve-requests 0` skips it), the roofline of the neuron loop,
 the clocks seen during the timed region and one oracle run on a host core.
@@ -268,26 +268,31 @@ def run_ours(args, rank, world, local_rank):
             # the other precision modes on the same workload, same timing rules
             # (reported beside the configured mixed-precision path)
             variants = {}
-            for prec in ("fp64", "mixed") if args.precision != "mixed" else ("fp64",):
-                if prec == args.precision:
-                    continue
-                with Extractor(device=local_rank, precision=prec, execution=args.execution) as vx:
-                    for _ in range(args.warmup):
-                        vx.extract(net, box, params=params_dev)
-                    vms = []
-                    for _ in range(args.steps):
-                        flush.zero_()
-                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                        e0.record()
-                        vx.extract(net, box, params=params_dev)
-                        e1.record()
-                        e1.synchronize()
-                        vms.append(e0.elapsed_time(e1))
-                    vc = vx.counts()
-                    vunits = vc["nV"] + vc["nE"]
-                variants[prec] = {"value": round(vunits * len(vms) / (sum(vms) / 1e3), 1), "unit": UNIT,
-                                  "ms_per_step": round(sum(vms) / len(vms), 4), "steps": len(vms),
-                                  "n_vertices": vc["nV"], "n_edges": vc["nE"]}
+            runs = [(p, {"precision": p}) for p in ("fp64", "mixed") if p != args.precision]
+            # level-set extraction with pruning during subdivision (its V + E are the
+            # pruned complex's)
+            runs.append(("prune", {"precision": args.precision, "prune": True}))
+            for name, kw in runs:
+                try:
+                    with Extractor(device=local_rank, execution=args.execution, **kw) as vx:
+                        for _ in range(args.warmup):
+                            vx.extract(net, box, params=params_dev)
+                        vms = []
+                        for _ in range(args.steps):
+                            flush.zero_()
+                            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                            e0.record()
+                            vx.extract(net, box, params=params_dev)
+                            e1.record()
+                            e1.synchronize()
+                            vms.append(e0.elapsed_time(e1))
+                        vc = vx.counts()
+                        vunits = vc["nV"] + vc["nE"]
+                    variants[name] = {"value": round(vunits * len(vms) / (sum(vms) / 1e3), 1), "unit": UNIT,
+                                      "ms_per_step": round(sum(vms) / len(vms), 4), "steps": len(vms),
+                                      "n_vertices": vc["nV"], "n_edges": vc["nE"], **kw}
+                except Exception as exc:  # a variant never takes the main line down
+                    variants[name] = {"error": str(exc)[:300], **kw}
             out["variants"] = variants
         if args.serve_requests > 0 and world == 1:
             lim = 1 << 30
