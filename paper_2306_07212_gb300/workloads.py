@@ -12,7 +12,8 @@ folded hyperplane, the last (output) layer included.
 Draw recipe: ``numpy.random.default_rng(seed)``; weights and biases are drawn in
 the order W1, b1, W2, b2, ... as float64 standard normals scaled by
 ``sqrt(2 / fan_in)`` (He-normal) and ``sqrt(bias_var)`` respectively; a bias
-variance of 0.01 gives a bias standard deviation of 0.1.
+variance of 0.01 gives a bias standard deviation of 0.1.  The counting sweep
+draws both uniformly on [-1/sqrt(fan_in), 1/sqrt(fan_in)] instead.
 """
 from __future__ import annotations
 
@@ -180,6 +181,41 @@ def random_mlp(D: int, depth: int, width: int, seed: int) -> tuple:
     """A generic random net: ``depth`` hidden layers of ``width`` and one output."""
     widths = [D] + [width] * depth + [1]
     return he_normal_mlp(widths, seed=seed), Box.cube(D)
+
+
+def default_uniform_mlp(widths: Sequence[int], seed: int) -> Net:
+    """Weights and biases uniform on [-1/sqrt(fan_in), 1/sqrt(fan_in)], float64.
+
+    This is the distribution of a freshly constructed fully-connected layer in
+    PyTorch (Kaiming-uniform with a = sqrt(5) gives the same bound for W).
+    Drawn in the order W1, b1, W2, b2, ... from ``default_rng(seed)``.
+    """
+    rng = np.random.default_rng(seed)
+    W, b = [], []
+    for l in range(len(widths) - 1):
+        fan_in, fan_out = int(widths[l]), int(widths[l + 1])
+        bound = 1.0 / math.sqrt(fan_in)
+        W.append(rng.uniform(-bound, bound, (fan_out, fan_in)))
+        b.append(rng.uniform(-bound, bound, fan_out))
+    return Net([int(w) for w in widths], W, b)
+
+
+COUNTING_DIMS = tuple(range(1, 11))
+COUNTING_WIDTHS = (10, 20, 40)
+COUNTING_SEEDS = 5
+
+
+def counting_sweep_net(D: int, width: int, seed: int) -> tuple:
+    """One point of the counting sweep of Section 5.1.2: a randomly initialised
+    net of four hidden layers of ``width`` and a scalar output, on [-1,1]^D.
+
+    The paper sweeps D = 1..10 and widths 10, 20, 40 with five random nets per
+    point and reports vertex and edge counts, run time and peak device memory.
+    The weights are drawn as a fresh PyTorch layer would draw them and rounded
+    once to FP32, so every precision mode extracts the same net.
+    """
+    widths = [D] + [width] * 4 + [1]
+    return default_uniform_mlp(widths, seed=seed).rounded_to_fp32(), Box.cube(D)
 
 
 @dataclasses.dataclass

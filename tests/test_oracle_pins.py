@@ -140,8 +140,17 @@ INV = [(2, [2, 12, 12, 1], 0), (2, [2, 16, 16, 16, 1], 1), (3, [3, 10, 10, 1], 2
 
 @pytest.mark.parametrize("D,widths,seed", INV)
 def test_invariants(D, widths, seed):
-    net = wl.he_normal_mlp(widths, seed=seed)
-    box = wl.Box.cube(D)
+    _check_invariants(wl.he_normal_mlp(widths, seed=seed), wl.Box.cube(D))
+
+
+@pytest.mark.parametrize("D,width,seed", [(2, 20, 0), (2, 40, 1), (3, 10, 2), (3, 20, 3), (4, 10, 4)])
+def test_invariants_counting_sweep_nets(D, width, seed):
+    # uniformly initialised nets of four hidden layers (Section 5.1.2)
+    _check_invariants(*wl.counting_sweep_net(D, width, seed))
+
+
+def _check_invariants(net, box):
+    D = net.D
     r = oracle.extract(net, box)
     assert r.status == 0, r.error
     m = 2 * D
