@@ -13,8 +13,11 @@ CUDA events.
 The JSON line also carries the FP64 mode and the pruned (level-set)
 extraction on the same workload (`variants`), the serving measurement (`serving`: a Poisson stream of
 2000 extraction requests through the batched 8-slot server and the plain
-1-slot path; `--serve-requests 0` skips it), the roofline of the neuron loop,
-the clocks seen during the timed region and one oracle run on a host core.
+1-slot path; `--serve-requests 0` skips it), the counting sweep of Section
+5.1.2 (`counting_sweep`: vertex and edge counts, time and peak device memory
+of random four-hidden-layer nets of widths 10, 20, 40 for D = 1..4, five nets
+per point; `--sweep-dims ''` skips it), the roofline of the neuron loop, the
+clocks seen during the timed region and one oracle run on a host core.
 
 --impl reference times the FP64 CPU oracle as the reference arm
 on the host cores.  Under torchrun (N > 1) every rank runs an independent
@@ -306,6 +309,12 @@ def run_ours(args, rank, world, local_rank):
                 except Exception as exc:  # the extraction numbers above stand on their own
                     serving[name] = {"slots": slots, "error": str(exc)[:300]}
             out["serving"] = serving
+        if args.sweep_dims and world == 1:
+            try:
+                out["counting_sweep"] = run_counting_sweep(_dims(args.sweep_dims), args.sweep_seeds, local_rank,
+                                                           args.precision, args.execution)
+            except Exception as exc:  # the extraction numbers above stand on their own
+                out["counting_sweep"] = {"error": str(exc)[:300]}
     ex.close()
     if dist:
         dist.destroy_process_group()
@@ -337,6 +346,68 @@ def run_serving(n_requests: int, slots: int, request_max_bytes: int):
             "ve_per_s": round(ve / span, 1), "completed": len(ok),
             "rejected": sum(r.status == 6 for r in res), "failed": sum(r.status not in (0, 6) for r in res),
             "errors": errors[:4]}
+
+
+def _dims(spec: str) -> list:
+    """"1-4" or "1,2,5" -> sorted input dimensions."""
+    dims = set()
+    for part in spec.split(","):
+        lo, _, hi = part.partition("-")
+        dims.update(range(int(lo), int(hi or lo) + 1))
+    return sorted(dims)
+
+
+def run_counting_sweep(dims, seeds: int, device: int, precision: str, execution: str):
+    """Counting sweep (Section 5.1.2): per input dimension D and width w, nets
+    of four hidden layers of w on [-1,1]^D, `seeds` random nets each; vertex
+    and edge counts, extraction time and peak device memory, mean and standard
+    deviation over the nets.  Each net gets a fresh context: `cold_ms` is its
+    first extraction (capacity growth included), `ms` the median of three more,
+    `peak_mib` the most device memory allocated above what was held before."""
+    import numpy as np
+    import torch
+    from paper_2306_07212_gb300 import Extractor, workloads
+
+    def timed(ex, net, box, params):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ex.extract(net, box, params=params)
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    def ms(a):
+        return [round(float(np.mean(a)), 3), round(float(np.std(a)), 3)]
+
+    t_start = time.perf_counter()
+    points = []
+    for width in workloads.COUNTING_WIDTHS:
+        for D in dims:
+            rows = []
+            try:
+                for seed in range(seeds):
+                    net, box = workloads.counting_sweep_net(D, width, seed)
+                    params = torch.from_numpy(net.flat_params()).cuda(device)
+                    torch.cuda.synchronize()
+                    base = torch.cuda.memory_allocated(device)
+                    torch.cuda.reset_peak_memory_stats(device)
+                    with Extractor(device=device, precision=precision, execution=execution) as ex:
+                        cold = timed(ex, net, box, params)
+                        peak = torch.cuda.max_memory_allocated(device) - base
+                        warm = statistics.median([timed(ex, net, box, params) for _ in range(3)])
+                        c = ex.counts()
+                    rows.append((c["nV"], c["nE"], cold, warm, peak / 2**20))
+            except Exception as exc:  # e.g. a dimension the library does not take
+                points.append({"D": D, "width": width, "error": str(exc)[:200]})
+                continue
+            a = np.array(rows, np.float64)
+            points.append({"D": D, "width": width, "nV": ms(a[:, 0]), "nE": ms(a[:, 1]), "ms": ms(a[:, 3]),
+                           "cold_ms": ms(a[:, 2]), "peak_mib": ms(a[:, 4]),
+                           "ve_per_s": round(float(np.mean((a[:, 0] + a[:, 1]) / (a[:, 3] / 1e3))), 1)})
+    return {"workload": f"Section 5.1.2 counting sweep: MLP [D, w, w, w, w, 1], w in "
+                        f"{list(workloads.COUNTING_WIDTHS)}, D in {dims}, {seeds} uniformly initialised nets per "
+                        f"point (FP32 weights), box [-1,1]^D, {precision} precision; values are [mean, std]",
+            "points": points, "seconds": round(time.perf_counter() - t_start, 1)}
 
 
 def cpu_baseline(net, box):
@@ -384,6 +455,9 @@ def main():
     ap.add_argument("--execution", default="persistent", choices=["persistent", "stepwise"])
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving stream to replay (0 = skip the serving measurement)")
+    ap.add_argument("--sweep-dims", default="1-4",
+                    help="input dimensions of the counting sweep, e.g. 1-4 or 1,2,5 ('' = skip it)")
+    ap.add_argument("--sweep-seeds", type=int, default=5, help="random nets per counting-sweep point")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -14,3 +14,9 @@ if HERE not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the compiled library")
     config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
+
+
+def pytest_collection_modifyitems(config, items):
+    # the counting sweep (sixty extractions up to 5e6 edges) runs after the
+    # faster GPU modules; the sort is stable, so every other order is kept
+    items.sort(key=lambda it: os.path.basename(str(it.fspath)) == "test_gpu_counting_sweep.py")

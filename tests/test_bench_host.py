@@ -1,0 +1,93 @@
+"""Host logic of bench.py's counting sweep, with CUDA and the library faked:
+the points it visits, the statistics it reports and a failing point that is
+recorded without ending the sweep."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import bench  # noqa: E402
+import paper_2306_07212_gb300 as pkg  # noqa: E402
+
+
+class _Clock:
+    t = 0.0
+
+
+class _Event:
+    def __init__(self, enable_timing=True):
+        self.at = None
+
+    def record(self):
+        _Clock.t += 2.0
+        self.at = _Clock.t
+
+    def synchronize(self):
+        pass
+
+    def elapsed_time(self, other):
+        return other.at - self.at
+
+
+class _FakeExtractor:
+    opened = []
+
+    def __init__(self, device, precision, execution):
+        self.args = (device, precision, execution)
+        _FakeExtractor.opened.append(self)
+        self.closed = False
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.closed = True
+
+    def extract(self, net, box, params=None):
+        if net.D > 8:
+            raise RuntimeError("input dimension must be in [1, 8]")
+        self.net = net
+
+    def counts(self):
+        w = self.net.widths[1]
+        return {"nV": 100 * self.net.D + w, "nE": 300 * self.net.D + w}
+
+
+@pytest.fixture
+def faked(monkeypatch):
+    monkeypatch.setattr(torch.cuda, "Event", _Event)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "memory_allocated", lambda *a, **k: 1 << 20)
+    monkeypatch.setattr(torch.cuda, "reset_peak_memory_stats", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "max_memory_allocated", lambda *a, **k: 3 << 20)
+    monkeypatch.setattr(torch.Tensor, "cuda", lambda self, *a, **k: self)
+    monkeypatch.setattr(pkg, "Extractor", _FakeExtractor)
+    _FakeExtractor.opened = []
+
+
+def test_dims_spec():
+    assert bench._dims("1-4") == [1, 2, 3, 4]
+    assert bench._dims("1,2,5") == [1, 2, 5]
+    assert bench._dims("2-3,7") == [2, 3, 7]
+
+
+def test_counting_sweep_points_and_statistics(faked):
+    out = bench.run_counting_sweep([1, 3], seeds=2, device=0, precision="mixed", execution="persistent")
+    pts = out["points"]
+    assert [(p["D"], p["width"]) for p in pts] == [(1, 10), (3, 10), (1, 20), (3, 20), (1, 40), (3, 40)]
+    # one fresh context per net, all closed again
+    assert len(_FakeExtractor.opened) == 12 and all(e.closed for e in _FakeExtractor.opened)
+    assert all(e.args == (0, "mixed", "persistent") for e in _FakeExtractor.opened)
+    p = pts[3]
+    assert p["nV"] == [320.0, 0.0] and p["nE"] == [920.0, 0.0]
+    assert p["ms"] == [2.0, 0.0] and p["cold_ms"] == [2.0, 0.0]
+    assert p["peak_mib"] == [2.0, 0.0]
+    assert p["ve_per_s"] == pytest.approx((320 + 920) / 2e-3)
+
+
+def test_counting_sweep_records_a_failing_point(faked):
+    out = bench.run_counting_sweep([8, 9], seeds=1, device=0, precision="mixed", execution="persistent")
+    by = {(p["D"], p["width"]): p for p in out["points"]}
+    assert "error" in by[(9, 10)] and "[1, 8]" in by[(9, 10)]["error"]
+    assert "error" not in by[(8, 40)] and by[(8, 40)]["nV"][0] == 840.0
+    assert len(out["points"]) == 6 and np.isfinite(out["seconds"])
