@@ -410,13 +410,29 @@ def run_counting_sweep(dims, seeds: int, device: int, precision: str, execution:
             "points": points, "seconds": round(time.perf_counter() - t_start, 1)}
 
 
+def host_cpu() -> dict:
+    """Core count and CPU model of the host that runs the oracle."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            key, _, val = line.partition(":")
+            if key.strip() == "Model name":
+                info["model"] = val.strip()
+                break
+    except Exception:
+        pass
+    return info
+
+
 def cpu_baseline(net, box):
     import oracle
     t0 = time.perf_counter()
     r = oracle.extract(net, box)
     dt = time.perf_counter() - t0
     return {"value": round((r.nV + r.nE) / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full FP64 oracle extraction of the same workload ({r.nV} V, {r.nE} E) in {dt:.2f} s"}
+            "sample": f"one full FP64 oracle extraction of the same workload ({r.nV} V, {r.nE} E) in {dt:.2f} s",
+            "host": host_cpu()}
 
 
 def run_reference(args, rank, world):
@@ -436,7 +452,7 @@ def run_reference(args, rank, world):
     total = sum(times)
     value = units * args.steps / total
     cpu = {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"full FP64 oracle extraction of the workload per step ({units} V+E)"}
+           "sample": f"full FP64 oracle extraction of the workload per step ({units} V+E)", "host": host_cpu()}
     return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / args.steps, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

@@ -91,3 +91,8 @@ def test_counting_sweep_records_a_failing_point(faked):
     assert "error" in by[(9, 10)] and "[1, 8]" in by[(9, 10)]["error"]
     assert "error" not in by[(8, 40)] and by[(8, 40)]["nV"][0] == 840.0
     assert len(out["points"]) == 6 and np.isfinite(out["seconds"])
+
+
+def test_host_cpu_reports_cores():
+    info = bench.host_cpu()
+    assert isinstance(info["nproc"], int) and info["nproc"] >= 1
