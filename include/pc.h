@@ -158,6 +158,36 @@ pc_status pc_set_allocator(pc_ctx *ctx, pc_alloc_fn alloc, pc_free_fn free_fn, v
 pc_status pc_extract(pc_ctx *ctx, int L, const int32_t *widths, const double *params,
                      const double *box_lo, const double *box_hi, void *stream);
 
+/* Edge subdivision on a polyhedral domain instead of a box (Section 4.1: a
+ * bounded domain given by m affine half-spaces; Section 5.2 suggests a
+ * simplex, whose vertex and edge counts grow linearly and quadratically with
+ * D instead of exponentially).  The domain is {x : c - A x >= 0}: A (m x D,
+ * row-major) and c (m) are host float64 arrays.  Its 1-skeleton is the
+ * caller's: X0 (nv0 x D, row-major, float64) and E0 (ne0 x 2 int32 vertex
+ * indices), host arrays, copied at the start of the call.  Sign-vector
+ * entry i < m is facet i (c_i - A_i x, + inside); the neurons follow at
+ * m, m + 1, ...  Facet i of an initial vertex is 0 when
+ * |c_i - A_i x| <= 1e-12 (|c_i| + sum_d |A_id x_d|), + otherwise.  As for
+ * the box, a facet's zero is perturbed only toward + in step (5).
+ * The domain must be a simple polytope and the skeleton complete:
+ *   - every vertex inside and on exactly D facets;
+ *   - every edge joins two distinct vertices sharing D - 1 facets;
+ *   - no edge twice, D edges at every vertex;
+ *   - a full-dimensional bounding box;
+ *   - D + 1 <= m and m + neurons <= 1024.
+ * Otherwise the call returns PC_ERR_INVALID before any device work.  The
+ * coordinate tolerance of the polish is relative to the diameter of the
+ * skeleton's bounding box.  Every other option, output and error is as for
+ * pc_extract. */
+pc_status pc_extract_domain(pc_ctx *ctx, int L, const int32_t *widths, const double *params, int m,
+                            const double *A, const double *c, int64_t nv0, const double *X0, int64_t ne0,
+                            const int32_t *E0, void *stream);
+
+/* The checks pc_extract_domain makes on a domain and its skeleton (host
+ * only, no device or context needed): PC_OK or PC_ERR_INVALID. */
+pc_status pc_check_domain(int D, int m, const double *A, const double *c, int64_t nv0, const double *X0,
+                          int64_t ne0, const int32_t *E0);
+
 /* Counts of the last extraction: vertices, edges, 64-bit words per sign
  * vector, input dimension D, and sign-vector entries (2D + neurons). */
 pc_status pc_counts(pc_ctx *ctx, int64_t *n_vertices, int64_t *n_edges, int32_t *sig_words,

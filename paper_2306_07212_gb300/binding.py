@@ -31,7 +31,7 @@ EXPORTS = ["pc_default_options", "pc_create", "pc_destroy", "pc_set_allocator", 
            "pc_diagnostics", "pc_kernel_times", "pc_error_estimates", "pc_values", "pc_extract_noalloc",
            "pc_estimate_bytes", "pc_server_default_options", "pc_server_create", "pc_server_submit",
            "pc_server_poll", "pc_server_error", "pc_server_wait_all", "pc_server_outputs", "pc_server_release", "pc_server_stats",
-           "pc_server_destroy", "pc_last_error", "pc_cell_counts"]
+           "pc_server_destroy", "pc_last_error", "pc_cell_counts", "pc_extract_domain", "pc_check_domain"]
 
 
 class PcError(RuntimeError):
@@ -112,6 +112,9 @@ def load_library(path: str = LIB):
                                            ctypes.c_int64, ctypes.c_int64, i64p, i64p, vp]
         lib.pc_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         lib.pc_cell_counts.argtypes = [vp, i64p, ctypes.c_int, i64p]
+        lib.pc_extract_domain.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp, ctypes.c_int64, vp,
+                                          ctypes.c_int64, vp, vp]
+        lib.pc_check_domain.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int64, vp, ctypes.c_int64, vp]
         lib.pc_last_error.argtypes = [vp]
         lib.pc_last_error.restype = ctypes.c_char_p
         for f in EXPORTS:
@@ -129,6 +132,26 @@ def _addr(x) -> Optional[int]:
     if isinstance(x, np.ndarray):
         return x.ctypes.data
     return int(x.data_ptr())
+
+
+def _domain_arrays(dom):
+    A = np.ascontiguousarray(dom.A, np.float64)
+    c = np.ascontiguousarray(dom.c, np.float64)
+    X0 = np.ascontiguousarray(dom.X0, np.float64)
+    E0 = np.ascontiguousarray(dom.E0, np.int32)
+    if A.ndim != 2 or c.shape != (A.shape[0],) or X0.ndim != 2 or X0.shape[1] != A.shape[1] or \
+            E0.ndim != 2 or E0.shape[1] != 2:
+        raise ValueError("domain arrays: A (m, D), c (m,), X0 (nv0, D), E0 (ne0, 2)")
+    return A, c, X0, E0
+
+
+def check_domain(dom) -> bool:
+    """pc_check_domain: whether pc_extract_domain accepts the domain and its
+    skeleton (host-only checks, no GPU needed)."""
+    A, c, X0, E0 = _domain_arrays(dom)
+    lib = load_library()
+    return lib.pc_check_domain(A.shape[1], A.shape[0], _addr(A), _addr(c), X0.shape[0], _addr(X0), E0.shape[0],
+                               _addr(E0)) == PC_OK
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -229,6 +252,22 @@ class Extractor:
         self.net = net
         st = self._lib.pc_extract(self._ctx, len(net.widths) - 1, _addr(widths), _addr(params),
                                   _addr(lo), _addr(hi), _stream_handle(stream))
+        self._check(st)
+        return self
+
+    def extract_domain(self, net, dom, params=None, stream=None) -> "Extractor":
+        """Runs pc_extract_domain on the polyhedral domain ``dom`` (A, c, X0,
+        E0: {x : c - A x >= 0} and its 1-skeleton, e.g. workloads.Polytope)."""
+        widths = np.ascontiguousarray(net.widths, np.int32)
+        if params is None:
+            params = np.ascontiguousarray(net.flat_params(), np.float64)
+        arrs = _domain_arrays(dom)
+        self._keep = (widths, params) + arrs
+        self.net = net
+        A, c, X0, E0 = arrs
+        st = self._lib.pc_extract_domain(self._ctx, len(net.widths) - 1, _addr(widths), _addr(params), A.shape[0],
+                                         _addr(A), _addr(c), X0.shape[0], _addr(X0), E0.shape[0], _addr(E0),
+                                         _stream_handle(stream))
         self._check(st)
         return self
 

@@ -116,6 +116,52 @@ __global__ void k_init(NetDesc net, State st) {
   }
 }
 
+// Step 0 on a polyhedral domain {x : c - A x >= 0} (Section 4.1, bounded
+// domains): the caller's 1-skeleton, vertices X0 (row-major nv0 x D) and
+// edges E0 (ne0 pairs of vertex indices), checked on the host before the
+// launch.  Facet entry i of a vertex is 0 when |c_i - A_i x| <= 1e-12 of
+// |c_i| + sum_d |A_id x_d| (the vertex lies on the facet), else +; every
+// neuron entry is unprocessed.
+__global__ void k_init_domain(NetDesc net, State st, const double* X0, const int32_t* E0, long long nv0,
+                              long long ne0) {
+  const int D = net.D, m = net.m;
+  const long long Vcap = st.Vcap;
+  for (long long v = threadIdx.x; v < nv0; v += blockDim.x) {
+    const double* x = X0 + v * D;
+    for (int d = 0; d < D; ++d) st.X[(long long)d * Vcap + v] = x[d];
+    for (int w = 0; w < net.S; ++w) {
+      uint64_t word = 0;
+      for (int k = 0; k < 32 && 32 * w + k < m; ++k) {
+        const int i = 32 * w + k;
+        double f = net.fc[i], s = fabs(net.fc[i]);
+        for (int d = 0; d < D; ++d) {
+          const double t = net.fA[(long long)i * D + d] * x[d];
+          f -= t;
+          s += fabs(t);
+        }
+        if (fabs(f) > 1e-12 * s) word |= kPlus << (2 * k);
+      }
+      st.SIG[(long long)w * Vcap + v] = word;
+    }
+    if (st.exc) st.exc[v] = 0.f;
+  }
+  for (long long e = threadIdx.x; e < ne0; e += blockDim.x) {
+    st.EU[e] = E0[2 * e];
+    st.EW[e] = E0[2 * e + 1];
+    if (st.deferred) st.vlist[e] = make_int4(0, 0, 0, 0);
+  }
+  if (threadIdx.x == 0) {
+    Counters c0{};
+    c0.nV_before = nv0;
+    c0.nE_before = ne0;
+    st.cnt[0] = c0;
+    Global g{};
+    g.halted_at = -1;
+    g.flip_at = -1;
+    *st.g = g;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Step (1) at the start of layer l: Z_l = W_l a + b_l for every vertex, with
 // a = x (l = 0) or a_k = z_k of layer l-1 if the vertex's entry is + else 0.
@@ -324,6 +370,7 @@ __global__ void __launch_bounds__(256) k_verify_pairs(NetDesc net, State st) {
 // dealt to warps round-robin.  n_stage: parameter pairs copied to shared
 // memory (all of them, or 0 when they do not fit; then they are read from
 // global memory, coalesced per layer).
+template <bool DOMAIN>
 __global__ void __launch_bounds__(kBlock) k_polish(NetDesc net, State st, float thr, int mw, long long n_stage) {
   // blockDim.x = 32 x (warps whose workspace fits kPolishSmemMax)
   extern __shared__ __align__(16) unsigned char psm[];
@@ -349,7 +396,7 @@ __global__ void __launch_bounds__(kBlock) k_polish(NetDesc net, State st, float 
       const int L = __ffs(flag) - 1;
       flag &= flag - 1;
       const long long u = base + L;
-      newton_ff_warp(net, st, P, u, net.P, mw, ws, zl[warp], &nout[warp]);
+      newton_ff_warp<DOMAIN>(net, st, P, u, net.P, mw, ws, zl[warp], &nout[warp]);
       if (nout[warp].ok) {
         if (lane < net.D) st.X[(long long)lane * Vcap + u] += nout[warp].dlt[lane];
         npol += (lane == 0);
@@ -649,8 +696,87 @@ static long long pow2_at_least(long long x) {
   return p;
 }
 
+// A polyhedral domain {x : c - A x >= 0} and its 1-skeleton, host arrays.
+struct DomainIn {
+  int m;
+  const double* A;    // m x D, row-major
+  const double* c;    // m
+  long long nv0;
+  const double* X0;   // nv0 x D, row-major
+  long long ne0;
+  const int32_t* E0;  // ne0 x 2
+};
+
+// Checks a domain and its skeleton for edge subdivision: finite values;
+// every vertex inside the domain and on exactly D facets (a simple polytope,
+// so that every vertex of the complex lies on D hyperplanes); every edge
+// joins two distinct vertices that share exactly D - 1 facets, no edge
+// twice, D edges at every vertex; a full-dimensional bounding box.  Returns
+// "" or the reason; on success lo / hi receive the bounding box.
+static std::string check_domain(int D, const DomainIn& d, double* lo, double* hi) {
+  if (D < 1 || D > kMaxD) return "input dimension must be in [1, 8]";
+  if (d.m < D + 1 || d.m > kMaxEntries) return "the number of facets must be in [D + 1, 1024]";
+  if (!d.A || !d.c || !d.X0 || !d.E0) return "null domain array";
+  if (d.nv0 < D + 1 || d.nv0 > (1ll << 20)) return "the skeleton needs D + 1 to 2^20 vertices";
+  if (d.ne0 < 1 || d.ne0 > (1ll << 23)) return "the skeleton needs 1 to 2^23 edges";
+  for (long long k = 0; k < (long long)d.m * D; ++k)
+    if (!std::isfinite(d.A[k])) return "non-finite facet normal";
+  for (int i = 0; i < d.m; ++i)
+    if (!std::isfinite(d.c[i])) return "non-finite facet offset";
+  const int zw = (d.m + 63) / 64;  // facet-zero bitmask words per vertex
+  std::vector<uint64_t> zeros(static_cast<size_t>(d.nv0) * zw, 0);
+  for (int k = 0; k < D; ++k) {
+    lo[k] = INFINITY;
+    hi[k] = -INFINITY;
+  }
+  for (long long v = 0; v < d.nv0; ++v) {
+    const double* x = d.X0 + v * D;
+    for (int k = 0; k < D; ++k) {
+      if (!std::isfinite(x[k])) return "non-finite vertex coordinate";
+      lo[k] = std::min(lo[k], x[k]);
+      hi[k] = std::max(hi[k], x[k]);
+    }
+    int nz = 0;
+    for (int i = 0; i < d.m; ++i) {
+      double f = d.c[i], s = std::fabs(d.c[i]);
+      for (int k = 0; k < D; ++k) {
+        const double t = d.A[(long long)i * D + k] * x[k];
+        f -= t;
+        s += std::fabs(t);
+      }
+      if (std::fabs(f) <= 1e-12 * s) {
+        zeros[v * zw + i / 64] |= 1ull << (i % 64);
+        ++nz;
+      } else if (f < 0) {
+        return "vertex " + std::to_string(v) + " lies outside facet " + std::to_string(i);
+      }
+    }
+    if (nz != D)
+      return "vertex " + std::to_string(v) + " lies on " + std::to_string(nz) + " facets, not D (a simple polytope is needed)";
+  }
+  for (int k = 0; k < D; ++k)
+    if (!(hi[k] > lo[k])) return "the skeleton is not full-dimensional";
+  std::vector<long long> deg(d.nv0, 0);
+  std::vector<std::pair<int32_t, int32_t>> pairs(d.ne0);
+  for (long long e = 0; e < d.ne0; ++e) {
+    const int32_t u = d.E0[2 * e], w = d.E0[2 * e + 1];
+    if (u < 0 || w < 0 || u >= d.nv0 || w >= d.nv0 || u == w) return "edge " + std::to_string(e) + " has a bad endpoint";
+    int shared = 0;
+    for (int q = 0; q < zw; ++q) shared += __builtin_popcountll(zeros[u * zw + q] & zeros[w * zw + q]);
+    if (shared != D - 1) return "edge " + std::to_string(e) + " does not lie on D - 1 facets";
+    ++deg[u];
+    ++deg[w];
+    pairs[e] = {std::min(u, w), std::max(u, w)};
+  }
+  for (long long v = 0; v < d.nv0; ++v)
+    if (deg[v] != D) return "vertex " + std::to_string(v) + " has " + std::to_string(deg[v]) + " edges, not D";
+  std::sort(pairs.begin(), pairs.end());
+  if (std::adjacent_find(pairs.begin(), pairs.end()) != pairs.end()) return "an edge occurs twice";
+  return "";
+}
+
 static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* params,
-                        const double* lo, const double* hi, bool deferred) {
+                        const double* lo, const double* hi, bool deferred, const DomainIn* dom = nullptr) {
   c->deferred = deferred ? 1 : 0;
   if (L < 1 || L > kMaxL) throw PcError(PC_ERR_INVALID, "number of layers must be in [1, 16]");
   const int D = widths[0];
@@ -659,7 +785,7 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   net = NetDesc{};
   net.L = L;
   net.D = D;
-  net.m = 2 * D;
+  net.m = dom ? dom->m : 2 * D;
   net.precision = c->opt.precision;
   net.kappa = static_cast<float>(c->opt.filter_kappa > 0 ? c->opt.filter_kappa : 2.0);
   long long p = 0;
@@ -681,12 +807,36 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   net.off[L] = n;
   net.N = n;
   net.P = net.m + n;
-  if (net.P > kMaxEntries) throw PcError(PC_ERR_INVALID, "2D + number of neurons must be <= 1024");
+  if (net.P > kMaxEntries) throw PcError(PC_ERR_INVALID, "facets + number of neurons must be <= 1024");
   net.S = (net.P + 31) / 32;
   for (int d = 0; d < D; ++d) {
     net.lo[d] = lo[d];
     net.hi[d] = hi[d];
     if (!(hi[d] > lo[d])) throw PcError(PC_ERR_INVALID, "box must have hi > lo");
+  }
+  // polyhedral domain: facets and skeleton in one device buffer (A, c, X0
+  // as float64, then E0); net.lo / net.hi hold the skeleton's bounding box
+  const double* X0dev = nullptr;
+  const int32_t* E0dev = nullptr;
+  if (dom) {
+    const size_t nA = (size_t)dom->m * D, nX = (size_t)dom->nv0 * D;
+    const size_t bytes = 8 * (nA + dom->m + nX) + 8 * (size_t)dom->ne0;
+    if (c->dom_cap < bytes || !c->dom_buf) {
+      c->dom_cap = 0;
+      ctx_free(c, c->dom_buf);
+      c->dom_buf = ctx_alloc(c, bytes);
+      if (!c->dom_buf) throw PcError(PC_ERR_OOM, "domain allocation failed");
+      c->dom_cap = bytes;
+    }
+    double* b = static_cast<double*>(c->dom_buf);
+    PC_CUDA(cudaMemcpyAsync(b, dom->A, 8 * nA, cudaMemcpyHostToDevice, c->stream));
+    PC_CUDA(cudaMemcpyAsync(b + nA, dom->c, 8 * (size_t)dom->m, cudaMemcpyHostToDevice, c->stream));
+    PC_CUDA(cudaMemcpyAsync(b + nA + dom->m, dom->X0, 8 * nX, cudaMemcpyHostToDevice, c->stream));
+    PC_CUDA(cudaMemcpyAsync(b + nA + dom->m + nX, dom->E0, 8 * (size_t)dom->ne0, cudaMemcpyHostToDevice, c->stream));
+    net.fA = b;
+    net.fc = b + nA;
+    X0dev = b + nA + dom->m;
+    E0dev = reinterpret_cast<const int32_t*>(b + nA + dom->m + nX);
   }
   c->hmax = hmax;
   c->mw = mw;
@@ -742,6 +892,8 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   } else {
     PC_CUDA(cudaMemsetAsync(c->bufs.table, 0xff, 16 * c->Tcap, c->stream));
   }
+  if (dom && (c->Vcap < dom->nv0 || c->Ecap < dom->ne0))
+    realloc_state(c, std::max(c->Vcap, dom->nv0), std::max(c->Ecap, dom->ne0), c->Tcap, false);
   PC_CUDA(cudaMemsetAsync(c->cnt, 0, sizeof(Counters) * (n + 1), c->stream));
 
   // launch geometry
@@ -752,7 +904,8 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   c->grid_step = std::min(kMaxGrid, 2 * c->num_sms);
 
   for (int k = 0; k <= pc_ctx::kPolishSlot; ++k) c->ev_used[k] = 0;
-  k_init<<<1, 256, 0, c->stream>>>(net, make_state(c));
+  if (dom) k_init_domain<<<1, 256, 0, c->stream>>>(net, make_state(c), X0dev, E0dev, dom->nv0, dom->ne0);
+  else k_init<<<1, 256, 0, c->stream>>>(net, make_state(c));
   PC_CUDA(cudaGetLastError());
   c->launches += 2;  // k_prep and k_init
 
@@ -811,7 +964,10 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     const size_t stage_b = (n_stage * 8 + 15) / 16 * 16;
     const int wpc = std::max(1, std::min(kWarps, int((kPolishSmemMax - stage_b) / ws)));
     TimerScope ts(c, pc_ctx::kPolishSlot);
-    k_polish<<<c->grid_step, 32 * wpc, stage_b + ws * wpc, c->stream>>>(net, make_state(c), thr, c->mw, n_stage);
+    if (dom)
+      k_polish<true><<<c->grid_step, 32 * wpc, stage_b + ws * wpc, c->stream>>>(net, make_state(c), thr, c->mw, n_stage);
+    else
+      k_polish<false><<<c->grid_step, 32 * wpc, stage_b + ws * wpc, c->stream>>>(net, make_state(c), thr, c->mw, n_stage);
     PC_CUDA(cudaGetLastError());
     c->launches += 1;
   }
@@ -894,7 +1050,8 @@ static cudaError_t set_func_attributes_now() {
   set((const void*)k_classify<double, false>, kNewtonSmemMax);
   set((const void*)k_classify<float, false>, kNewtonSmemMax);
   set((const void*)k_classify<float, true>, kNewtonSmemMax);
-  set((const void*)k_polish, kPolishSmemMax);
+  set((const void*)k_polish<false>, kPolishSmemMax);
+  set((const void*)k_polish<true>, kPolishSmemMax);
   {
     const cudaError_t r = pc_gemm_tc_set_attributes();
     if (e == cudaSuccess) e = r;
@@ -971,6 +1128,7 @@ pc_status pc_destroy(pc_ctx* c) {
   ctx_free(c, c->cnt);
   ctx_free(c, c->g);
   ctx_free(c, c->cta);
+  ctx_free(c, c->dom_buf);
   c->release_extra();
   cudaStreamSynchronize(c->stream);
   for (auto& e : c->ev) {
@@ -1007,6 +1165,44 @@ pc_status pc_extract(pc_ctx* c, int L, const int32_t* widths, const double* para
       // again with every pairing verified before it is made
       c->reruns += 1;
       run_extract(c, L, widths, params, lo, hi, false);
+    }
+    return PC_OK;
+  } catch (const PcError& e) {
+    cudaGetLastError();
+    cudaStreamSynchronize(c->stream);
+    c->have_result = false;
+    return c->fail(e.status, e.what());
+  } catch (const std::exception& e) {
+    c->have_result = false;
+    return c->fail(PC_ERR_INVALID, e.what());
+  }
+}
+
+pc_status pc_check_domain(int D, int m, const double* A, const double* cvec, int64_t nv0, const double* X0,
+                          int64_t ne0, const int32_t* E0) {
+  double lo[kMaxD], hi[kMaxD];
+  const DomainIn dom{m, A, cvec, nv0, X0, ne0, E0};
+  return check_domain(D, dom, lo, hi).empty() ? PC_OK : PC_ERR_INVALID;
+}
+
+pc_status pc_extract_domain(pc_ctx* c, int L, const int32_t* widths, const double* params, int m, const double* A,
+                            const double* cvec, int64_t nv0, const double* X0, int64_t ne0, const int32_t* E0,
+                            void* stream) {
+  if (!c || !widths || !params || L < 1) return PC_ERR_INVALID;
+  c->err.clear();
+  c->have_result = false;
+  const DomainIn dom{m, A, cvec, nv0, X0, ne0, E0};
+  double lo[kMaxD], hi[kMaxD];
+  const std::string why = check_domain(widths[0], dom, lo, hi);
+  if (!why.empty()) return c->fail(PC_ERR_INVALID, "domain: " + why);
+  try {
+    PC_CUDA(cudaSetDevice(c->device));
+    c->stream = static_cast<cudaStream_t>(stream);
+    try {
+      run_extract(c, L, widths, params, lo, hi, c->opt.pairing == PC_PAIR_DEFERRED, &dom);
+    } catch (const NeedsInlinePairing&) {
+      c->reruns += 1;
+      run_extract(c, L, widths, params, lo, hi, false, &dom);
     }
     return PC_OK;
   } catch (const PcError& e) {
@@ -1281,7 +1477,7 @@ extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const doub
       const long long n_stage = polish_stage(p, ws);
       const size_t stage_b = (n_stage * 8 + 15) / 16 * 16;
       const int wpc = std::max(1, std::min(kWarps, int((kPolishSmemMax - stage_b) / ws)));
-      k_polish<<<c.grid_step, 32 * wpc, stage_b + ws * wpc, c.stream>>>(net, make_state(&c), thr, c.mw, n_stage);
+      k_polish<false><<<c.grid_step, 32 * wpc, stage_b + ws * wpc, c.stream>>>(net, make_state(&c), thr, c.mw, n_stage);
       PC_CUDA(cudaGetLastError());
     }
     Global g{};

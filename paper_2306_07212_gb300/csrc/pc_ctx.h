@@ -86,6 +86,10 @@ struct pc_ctx {
   void* h_cnt = nullptr;
   void* h_g = nullptr;
 
+  // polyhedral domain of the last extraction (facets and initial skeleton)
+  void* dom_buf = nullptr;
+  size_t dom_cap = 0;
+
   int deferred = 0;  // this extraction pairs by fingerprint (checked after)
   int reruns = 0;    // extractions repeated with inline face verification
 

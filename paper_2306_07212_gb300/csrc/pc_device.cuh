@@ -69,6 +69,12 @@ struct NetDesc {
   const float* norms;    // per layer: [2l] = max_j ||W_j||_2, [2l+1] = max_j |b_j|
   const float* nrm;      // per neuron n: [3n] = ||W_n||_2, [3n+1] = |b_n|, [3n+2] = 1/||W_n||_2
   float kappa;           // filter factor
+  // Polyhedral domain {x : c - A x >= 0} (Section 4.1): facet i of the m
+  // entries has the value fc[i] - fA[i, :] x (fA row-major m x D, device).
+  // Both null for the box [lo, hi], whose facet 2d is x_d - lo_d and 2d+1
+  // is hi_d - x_d.
+  const double* fA;
+  const double* fc;
 };
 
 struct Counters {        // 128 bytes

@@ -35,8 +35,34 @@ struct NewtonOut {
   int pad;
 };
 
-// One Newton step on the D zero entries of vertex v: rows are the facets'
-// (+-e_d, value from the stored coordinate) and the neurons' (gradient A,
+// Added to a polyhedral domain's facet entry in a zero list once its row is
+// in A / gv: newton_solve then takes it like a neuron's row.
+constexpr int kFacetRow = 1 << 20;
+
+// Rows of a polyhedral domain's facets among the zero entries s_zl[0, nzc)
+// of vertex v: facet j has the value c_j - A_j x (x the stored coordinates)
+// and the gradient -A_j; they go to the same rows A (q * D + d) and values
+// gv[q] as the neurons', and the entry becomes j + kFacetRow (thread q of
+// the group handles entry q).
+__device__ inline void domain_facet_rows(const NetDesc& net, const State& st, long long v, int* s_zl, int nzc,
+                                         int q, double* A, double* gv) {
+  if (net.fA == nullptr || q >= nzc) return;
+  const int j = s_zl[q];
+  if (j >= net.m) return;
+  const int D = net.D;
+  const double* a = net.fA + (long long)j * D;
+  double f = net.fc[j];
+  for (int dd = 0; dd < D; ++dd) {
+    f -= a[dd] * st.X[(long long)dd * st.Vcap + v];
+    A[q * D + dd] = -a[dd];
+  }
+  gv[q] = f;
+  s_zl[q] = j + kFacetRow;
+}
+
+// One Newton step on the D zero entries of vertex v: rows are the box
+// facets' (+-e_d, value from the stored coordinate) and the neurons' and a
+// polyhedral domain's facets' (gradient A,
 // value gv); Gaussian elimination with partial pivoting in T.  The residuals
 // are formed in float64; the step is small (the stored coordinates are
 // FP32-accurate), so solving for it in float32 (the polish) loses only
@@ -213,6 +239,10 @@ __device__ void newton_group(const NetDesc& net, const State& st, long long v, i
     float* t1 = J; J = Jn; Jn = t1;
     in = H;
   }
+  if (net.fA != nullptr) {
+    domain_facet_rows(net, st, v, s_zl, nzc, tid, A, gv);
+    if (WARP) __syncwarp(); else __syncthreads();
+  }
   if (tid == 0) {
     NewtonOut o{};
     o.nz = nz;
@@ -260,6 +290,9 @@ __host__ __device__ constexpr int ff_ws_bytes(int mw, int D) {
 // parameters in the WT2 layout, in global or shared memory.  ws:
 // ff_ws_bytes(mw, D) bytes of shared memory private to the warp, 8-byte
 // aligned; s_zl: kMaxD + 2 ints.
+// DOMAIN: the facets are a polyhedral domain's (net.fA), not the box's; a
+// separate instantiation, so the box polish compiles as if it had none.
+template <bool DOMAIN>
 __device__ void newton_ff_warp(const NetDesc& net, const State& st, const float2* P, long long v, int e_end,
                                int mw, unsigned char* ws, int* s_zl, NewtonOut* out) {
   const int lane = threadIdx.x & 31;
@@ -359,6 +392,10 @@ __device__ void newton_ff_warp(const NetDesc& net, const State& st, const float2
     float* t1 = alo; alo = nlo; nlo = t1;
     float* t2 = J; J = Jn; Jn = t2;
     in = H;
+  }
+  if (DOMAIN) {
+    domain_facet_rows(net, st, v, s_zl, nzc, lane, A, gv);
+    __syncwarp();
   }
   if (lane == 0) {
     NewtonOut o{};

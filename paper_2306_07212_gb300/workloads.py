@@ -141,6 +141,26 @@ class Polytope:
         return Polytope(A, c, X0, E0)
 
     @staticmethod
+    def corner_cut(D: int) -> "Polytope":
+        """[-1,1]^D without the corner (1, ..., 1): the box's 2D half-spaces
+        and sum_d x_d <= D - 1.  A simple polytope with the 2^D - 1 remaining
+        corners and D new vertices (1, ..., 1 with one coordinate 0)."""
+        box = Polytope.from_box(Box.cube(D))
+        A = np.vstack([box.A, np.ones((1, D))])
+        c = np.concatenate([box.c, [D - 1.0]])
+        full = (1 << D) - 1
+        keep = [k for k in range(1 << D) if k != full]
+        rank = {k: r for r, k in enumerate(keep)}
+        X0 = [box.X0[k] for k in keep]
+        E0 = [(rank[u], rank[w]) for u, w in box.E0 if full not in (u, w)]
+        for d in range(D):
+            X0.append(np.where(np.arange(D) == d, 0.0, 1.0))
+            E0.append((rank[full ^ (1 << d)], len(X0) - 1))  # the cut edge toward the removed corner
+        first = len(keep)
+        E0 += [(first + i, first + j) for i in range(D) for j in range(i + 1, D)]
+        return Polytope(A, c, np.array(X0), np.array(E0, np.int32))
+
+    @staticmethod
     def from_box(box: "Box") -> "Polytope":
         """The box as 2D half-spaces (2d: x_d - lo_d >= 0, 2d+1: hi_d - x_d >= 0)
         with its corners (corner c has coordinate d at hi iff bit d of c is set)

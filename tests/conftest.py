@@ -16,7 +16,11 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
 
 
+# GPU modules that run after all the others, in this order: the counting
+# sweep (sixty extractions up to 5e6 edges), then the polyhedral domains
+_LAST = {"test_gpu_counting_sweep.py": 1, "test_gpu_domains.py": 2}
+
+
 def pytest_collection_modifyitems(config, items):
-    # the counting sweep (sixty extractions up to 5e6 edges) runs after the
-    # faster GPU modules; the sort is stable, so every other order is kept
-    items.sort(key=lambda it: os.path.basename(str(it.fspath)) == "test_gpu_counting_sweep.py")
+    # the sort is stable, so every other order is kept
+    items.sort(key=lambda it: _LAST.get(os.path.basename(str(it.fspath)), 0))

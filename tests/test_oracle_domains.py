@@ -65,3 +65,27 @@ def test_line_arrangement_in_a_triangle(n, seed):
             I += 1
     assert r.nV == 3 + 2 * n_in + I
     assert len(r.E) == 3 + 3 * n_in + 2 * I
+
+
+# --- a domain that is neither a box nor a simplex ---------------------------
+
+@pytest.mark.parametrize("widths", [[2, 4, 3, 1], [2, 3, 3, 3, 1], [3, 4, 3, 1], [3, 3, 3, 1], [2, 6, 1]])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_corner_cut_cube_matches_brute_force(widths, seed):
+    net = wl.he_normal_mlp(widths, seed=700 + seed)
+    dom = wl.Polytope.corner_cut(widths[0])
+    r = oracle.extract_domain(net, dom)
+    b = oracle.brute_domain(net, dom, tol=1e-9)
+    assert r.status == 0 and b.status == 0, (r.error, b.error)
+    assert_same_complex((r.X, r.S, r.E), (b.X, b.S, b.E), coord_tol=1e-9, what=f"corner cut {widths} seed {seed}")
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 4])
+def test_corner_cut_skeleton_and_euler_characteristic(D):
+    dom = wl.Polytope.corner_cut(D)
+    assert len(dom.X0) == 2 ** D - 1 + D
+    assert len(dom.E0) == D * 2 ** (D - 1) + D * (D - 1) // 2
+    assert np.all(np.bincount(dom.E0.ravel(), minlength=len(dom.X0)) == D)
+    r = oracle.extract_domain(wl.he_normal_mlp([D, 8, 8, 1], seed=D), dom)
+    f, chi = oracle.faces(r)
+    assert r.status == 0 and chi == 1
