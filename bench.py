@@ -16,7 +16,8 @@ extraction on the same workload (`variants`), the serving measurement (`serving`
 1-slot path; `--serve-requests 0` skips it), the counting sweep of Section
 5.1.2 (`counting_sweep`: vertex and edge counts, time and peak device memory
 of random four-hidden-layer nets of widths 10, 20, 40 for D = 1..4, five nets
-per point; `--sweep-dims ''` skips it), the roofline of the neuron loop, the
+per point; `--sweep-dims ''` skips it), the same net on a simplex domain
+(`domain`; `--domain 0` skips it), the roofline of the neuron loop, the
 clocks seen during the timed region and one oracle run on a host core.
 
 --impl reference times the FP64 CPU oracle as the reference arm
@@ -315,6 +316,11 @@ def run_ours(args, rank, world, local_rank):
                                                            args.precision, args.execution)
             except Exception as exc:  # the extraction numbers above stand on their own
                 out["counting_sweep"] = {"error": str(exc)[:300]}
+        if args.domain and world == 1:
+            try:
+                out["domain"] = run_domain(net, params_dev, flush, local_rank, args)
+            except Exception as exc:
+                out["domain"] = {"error": str(exc)[:300]}
     ex.close()
     if dist:
         dist.destroy_process_group()
@@ -346,6 +352,33 @@ def run_serving(n_requests: int, slots: int, request_max_bytes: int):
             "ve_per_s": round(ve / span, 1), "completed": len(ok),
             "rejected": sum(r.status == 6 for r in res), "failed": sum(r.status not in (0, 6) for r in res),
             "errors": errors[:4]}
+
+
+def run_domain(net, params_dev, flush, device: int, args):
+    """The workload's net on a polyhedral domain instead of the box (Section
+    4.1; Section 5.2 suggests a simplex): the corner simplex of the box,
+    x_d >= -1 and sum_d (x_d + 1) <= 2, same timing rules as the main line."""
+    import torch
+    from paper_2306_07212_gb300 import Extractor, workloads
+    dom = workloads.Polytope.simplex(net.D)
+    with Extractor(device=device, precision=args.precision, execution=args.execution) as dx:
+        for _ in range(args.warmup):
+            dx.extract_domain(net, dom, params=params_dev)
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            dx.extract_domain(net, dom, params=params_dev)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        c = dx.counts()
+    units = c["nV"] + c["nE"]
+    return {"workload": f"same net on the simplex x_d >= -1, sum_d (x_d + 1) <= 2 ({len(dom.X0)} vertices, "
+                        f"{len(dom.c)} facets)", "value": round(units * len(ms) / (sum(ms) / 1e3), 1), "unit": UNIT,
+            "ms_per_step": round(sum(ms) / len(ms), 4), "steps": len(ms), "n_vertices": c["nV"],
+            "n_edges": c["nE"]}
 
 
 def _dims(spec: str) -> list:
@@ -474,6 +507,7 @@ def main():
     ap.add_argument("--sweep-dims", default="1-4",
                     help="input dimensions of the counting sweep, e.g. 1-4 or 1,2,5 ('' = skip it)")
     ap.add_argument("--sweep-seeds", type=int, default=5, help="random nets per counting-sweep point")
+    ap.add_argument("--domain", type=int, default=1, help="1: also time the net on a simplex domain")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

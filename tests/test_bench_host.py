@@ -52,6 +52,10 @@ class _FakeExtractor:
         w = self.net.widths[1]
         return {"nV": 100 * self.net.D + w, "nE": 300 * self.net.D + w}
 
+    def extract_domain(self, net, dom, params=None):
+        assert dom.A.shape[1] == net.D
+        self.net = net
+
 
 @pytest.fixture
 def faked(monkeypatch):
@@ -96,3 +100,22 @@ def test_counting_sweep_records_a_failing_point(faked):
 def test_host_cpu_reports_cores():
     info = bench.host_cpu()
     assert isinstance(info["nproc"], int) and info["nproc"] >= 1
+
+
+def test_domain_measurement(faked):
+    from paper_2306_07212_gb300 import workloads as wl
+
+    class Args:
+        precision, execution, warmup, steps = "mixed", "persistent", 3, 4
+
+    class Flush:
+        def zero_(self):
+            pass
+
+    net = wl.he_normal_mlp([3, 16, 16, 1], seed=0)
+    out = bench.run_domain(net, None, Flush(), 0, Args())
+    assert out["steps"] == 4 and out["ms_per_step"] == 2.0
+    assert (out["n_vertices"], out["n_edges"]) == (316, 916)
+    assert out["value"] == pytest.approx((316 + 916) / 2e-3)
+    assert "4 vertices, 4 facets" in out["workload"]
+    assert len(_FakeExtractor.opened) == 1 and _FakeExtractor.opened[0].closed
