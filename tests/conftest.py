@@ -17,8 +17,9 @@ def pytest_configure(config):
 
 
 # GPU modules that run after all the others, in this order: the counting
-# sweep (sixty extractions up to 5e6 edges), then the polyhedral domains
-_LAST = {"test_gpu_counting_sweep.py": 1, "test_gpu_domains.py": 2}
+# sweep (sixty extractions up to 5e6 edges), the polyhedral domains, then the
+# counting sweep at D = 5 and 6
+_LAST = {"test_gpu_counting_sweep.py": 1, "test_gpu_domains.py": 2, "test_gpu_counting_sweep_high_dims.py": 3}
 
 
 def pytest_collection_modifyitems(config, items):
