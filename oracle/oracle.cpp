@@ -41,6 +41,30 @@
 //     counted and treated as +.
 //   * Edge sign vector = join of its endpoints (entrywise: the nonzero value
 //     where one is 0, the common value otherwise).
+//
+// What pins each function to something other than itself (CPU tests):
+//   orc_extract   the brute force on tiny deep nets; the clipped
+//                 line-arrangement closed form V = 4 + 2n + I, E = 4 + 3n + 2I;
+//                 C(n, D) interior vertices of a generic arrangement; the
+//                 clipped-arrangement vertex census; an independent
+//                 layer-by-layer breakpoint scan at D = 1; zero counts,
+//                 degrees and bookkeeping of Section 4.1; the zero residual
+//                 of Section 5.1.1 and a direct D x D solve; invariance under
+//                 neuron permutation and positive rescaling; the paper's
+//                 printed 2D counts against the line-arrangement identity.
+//   orc_faces     the region count of clipped generic arrangements (1 + the
+//                 k-subsets whose flat meets the open domain, by a linear
+//                 program per flat) and Euler characteristic 1.
+//   orc_brute     the definition itself; it agrees with orc_extract and
+//                 with the closed forms above.
+//   orc_grad      central finite differences of FP64 extractions.
+//   domains       the box as half-spaces reproduces the box bit for bit;
+//                 brute force on simplices and a corner-cut cube; the line
+//                 arrangement in a triangle; Euler characteristic 1.
+//   pruning       a sub-complex of the full extraction with the same level
+//                 set, equal to the brute-force level set on tiny nets.
+// No function is parity unpinned.  The vertex and edge counts of the
+// benchmark workloads themselves are: the paper prints none for them.
 
 #include <algorithm>
 #include <array>
