@@ -381,6 +381,33 @@ def run_domain(net, params_dev, flush, device: int, args):
             "n_edges": c["nE"]}
 
 
+def zero_residual(net, box, X, words) -> float:
+    """Section 5.1.1's validation: the largest |value| of a vertex's zero
+    entries (facets and neuron pre-activations by a float64 forward pass at
+    its coordinates), relative to the box's extent.  X: (nV, D) float64;
+    words: (S, nV) packed sign vectors (entry j at bits 2 (j mod 32) of word
+    j / 32, 00 = 0)."""
+    import numpy as np
+    X = np.asarray(X, np.float64)
+    words = np.asarray(words, np.uint64)
+    vals = [X - box.lo, box.hi - X]
+    facets = np.empty((len(X), 2 * net.D))
+    facets[:, 0::2], facets[:, 1::2] = vals
+    cols, a = [facets], X
+    for W, b in zip(net.W, net.b):
+        z = a @ W.T + b
+        cols.append(z)
+        a = np.maximum(z, 0.0)
+    allv = np.concatenate(cols, axis=1)
+    worst = 0.0
+    for j in range(allv.shape[1]):
+        code = (words[j // 32] >> np.uint64(2 * (j % 32))) & np.uint64(3)
+        on = code == 0
+        if on.any():
+            worst = max(worst, float(np.abs(allv[on, j]).max()))
+    return worst / float(np.max(box.hi - box.lo))
+
+
 def _dims(spec: str) -> list:
     """"1-4" or "1,2,5" -> sorted input dimensions."""
     dims = set()
@@ -396,7 +423,9 @@ def run_counting_sweep(dims, seeds: int, device: int, precision: str, execution:
     and edge counts, extraction time and peak device memory, mean and standard
     deviation over the nets.  Each net gets a fresh context: `cold_ms` is its
     first extraction (capacity growth included), `ms` the median of three more,
-    `peak_mib` the most device memory allocated above what was held before."""
+    `peak_mib` the most device memory allocated above what was held before;
+    at width 10 (the paper's validation nets) `zero_residual_rel` is the
+    largest zero-entry residual over the nets (zero_residual)."""
     import numpy as np
     import torch
     from paper_2306_07212_gb300 import Extractor, workloads
@@ -416,7 +445,7 @@ def run_counting_sweep(dims, seeds: int, device: int, precision: str, execution:
     points = []
     for width in workloads.COUNTING_WIDTHS:
         for D in dims:
-            rows = []
+            rows, residual = [], 0.0
             try:
                 for seed in range(seeds):
                     net, box = workloads.counting_sweep_net(D, width, seed)
@@ -429,6 +458,8 @@ def run_counting_sweep(dims, seeds: int, device: int, precision: str, execution:
                         peak = torch.cuda.max_memory_allocated(device) - base
                         warm = statistics.median([timed(ex, net, box, params) for _ in range(3)])
                         c = ex.counts()
+                        if width == 10:  # the paper's validation net: four layers of width 10
+                            residual = max(residual, zero_residual(net, box, ex.vertices(), ex.sign_words()))
                     rows.append((c["nV"], c["nE"], cold, warm, peak / 2**20))
             except Exception as exc:  # e.g. a dimension the library does not take
                 points.append({"D": D, "width": width, "error": str(exc)[:200]})
@@ -437,6 +468,8 @@ def run_counting_sweep(dims, seeds: int, device: int, precision: str, execution:
             points.append({"D": D, "width": width, "nV": ms(a[:, 0]), "nE": ms(a[:, 1]), "ms": ms(a[:, 3]),
                            "cold_ms": ms(a[:, 2]), "peak_mib": ms(a[:, 4]),
                            "ve_per_s": round(float(np.mean((a[:, 0] + a[:, 1]) / (a[:, 3] / 1e3))), 1)})
+            if width == 10:
+                points[-1]["zero_residual_rel"] = float(f"{residual:.3g}")
     return {"workload": f"Section 5.1.2 counting sweep: MLP [D, w, w, w, w, 1], w in "
                         f"{list(workloads.COUNTING_WIDTHS)}, D in {dims}, {seeds} uniformly initialised nets per "
                         f"point (FP32 weights), box [-1,1]^D, {precision} precision; values are [mean, std]",

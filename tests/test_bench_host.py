@@ -52,6 +52,13 @@ class _FakeExtractor:
         w = self.net.widths[1]
         return {"nV": 100 * self.net.D + w, "nE": 300 * self.net.D + w}
 
+    def vertices(self):
+        return np.zeros((self.counts()["nV"], self.net.D))
+
+    def sign_words(self):
+        S = (2 * self.net.D + self.net.n_neurons + 31) // 32
+        return np.full((S, self.counts()["nV"]), 0x5555555555555555, np.uint64)  # every entry +
+
     def extract_domain(self, net, dom, params=None):
         assert dom.A.shape[1] == net.D
         self.net = net
@@ -82,6 +89,8 @@ def test_counting_sweep_points_and_statistics(faked):
     # one fresh context per net, all closed again
     assert len(_FakeExtractor.opened) == 12 and all(e.closed for e in _FakeExtractor.opened)
     assert all(e.args == (0, "mixed", "persistent") for e in _FakeExtractor.opened)
+    assert all(("zero_residual_rel" in p) == (p["width"] == 10) for p in pts)
+    assert pts[0]["zero_residual_rel"] == 0.0
     p = pts[3]
     assert p["nV"] == [320.0, 0.0] and p["nE"] == [920.0, 0.0]
     assert p["ms"] == [2.0, 0.0] and p["cold_ms"] == [2.0, 0.0]
@@ -119,3 +128,25 @@ def test_domain_measurement(faked):
     assert out["value"] == pytest.approx((316 + 916) / 2e-3)
     assert "4 vertices, 4 facets" in out["workload"]
     assert len(_FakeExtractor.opened) == 1 and _FakeExtractor.opened[0].closed
+
+
+def _pack(S):
+    """int8 sign vectors (nV, P) -> packed 2-bit words (ceil(P / 32), nV)."""
+    nV, P = S.shape
+    words = np.zeros(((P + 31) // 32, nV), np.uint64)
+    for j in range(P):
+        code = np.where(S[:, j] == 1, 1, np.where(S[:, j] == -1, 2, 0)).astype(np.uint64)
+        words[j // 32] |= code << np.uint64(2 * (j % 32))
+    return words
+
+
+def test_zero_residual_of_an_exact_complex_and_a_shifted_one():
+    import oracle
+    from paper_2306_07212_gb300 import workloads as wl
+    net, box = wl.counting_sweep_net(3, 10, seed=1)
+    r = oracle.extract(net, box)
+    words = _pack(r.S)
+    assert bench.zero_residual(net, box, r.X, words) < 1e-13
+    X = r.X.copy()
+    X[5] += 1e-4  # one vertex moved off its zero set
+    assert 1e-6 < bench.zero_residual(net, box, X, words) < 1e-3
