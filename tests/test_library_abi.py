@@ -77,3 +77,21 @@ def test_memory_estimate_covers_the_oracle_complex(lib_path):
     small = estimate_bytes(wl.he_normal_mlp([3, 16, 16, 1], seed=0))
     assert estimate_bytes(wl.he_normal_mlp([3, 32, 16, 1], seed=0)) > small
     assert estimate_bytes(wl.he_normal_mlp([3, 16, 16, 16, 1], seed=0)) > small
+
+
+def test_header_is_plain_c_and_host_calls_work(lib_path, tmp_path):
+    """include/pc.h compiles as strict C99 (-Wall -Wextra -Werror -pedantic);
+    a C program links libpc.so and calls the entry points that need no GPU."""
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path / "abi_host")
+    src = os.path.join(ROOT, "tests", "c", "abi_host.c")
+    libdir = os.path.dirname(lib_path)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I" + os.path.join(ROOT, "include"),
+                        src, "-L" + libdir, "-lpc", "-Wl,-rpath," + libdir, "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.strip().endswith("ok")
