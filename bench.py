@@ -15,7 +15,7 @@ extraction on the same workload (`variants`), the serving measurement (`serving`
 2000 extraction requests through the batched 8-slot server and the plain
 1-slot path; `--serve-requests 0` skips it), the counting sweep of Section
 5.1.2 (`counting_sweep`: vertex and edge counts, time and peak device memory
-of random four-hidden-layer nets of widths 10, 20, 40 for D = 1..4, five nets
+of random four-hidden-layer nets of widths 10, 20, 40 for D = 1..5, five nets
 per point; `--sweep-dims ''` skips it), the same net on a simplex domain
 (`domain`; `--domain 0` skips it), the roofline of the neuron loop, the
 clocks seen during the timed region and one oracle run on a host core.
@@ -537,7 +537,7 @@ def main():
     ap.add_argument("--execution", default="persistent", choices=["persistent", "stepwise"])
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving stream to replay (0 = skip the serving measurement)")
-    ap.add_argument("--sweep-dims", default="1-4",
+    ap.add_argument("--sweep-dims", default="1-5",
                     help="input dimensions of the counting sweep, e.g. 1-4 or 1,2,5 ('' = skip it)")
     ap.add_argument("--sweep-seeds", type=int, default=5, help="random nets per counting-sweep point")
     ap.add_argument("--domain", type=int, default=1, help="1: also time the net on a simplex domain")
