@@ -9,7 +9,10 @@ at D = 6, width 20; the next dimension would take hours and more host
 memory than a workstation has); a point is left out when one of its
 extractions takes longer than --max-seconds.
 
-  python tests/golden/make_counting_sweep.py [--max-seconds 600]
+  python tests/golden/make_counting_sweep.py [--max-seconds 600] [--only 5:40 ...]
+
+--only recomputes the listed D:width points and merges them into the
+existing file.
 """
 import argparse
 import json
@@ -31,12 +34,16 @@ MAX_DIM = {10: 6, 20: 6, 40: 5}
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--max-seconds", type=float, default=600.0)
+    ap.add_argument("--only", nargs="*", default=None, help="D:width points to recompute and merge")
     args = ap.parse_args()
+    only = None if args.only is None else {tuple(int(x) for x in p.split(":")) for p in args.only}
     points = []
     for width in wl.COUNTING_WIDTHS:
         for D in wl.COUNTING_DIMS:
             if D > MAX_DIM[width]:
                 break
+            if only is not None and (D, width) not in only:
+                continue
             rows, slow = [], False
             for seed in range(wl.COUNTING_SEEDS):
                 net, box = wl.counting_sweep_net(D, width, seed)
@@ -53,6 +60,10 @@ def main():
             if slow:
                 break  # larger D at this width only takes longer
             points.append({"D": D, "width": width, "counts": rows})
+    if only is not None:
+        with open(OUT) as f:
+            kept = [p for p in json.load(f)["points"] if (p["D"], p["width"]) not in only]
+        points = sorted(kept + points, key=lambda p: (wl.COUNTING_WIDTHS.index(p["width"]), p["D"]))
     doc = {"source": "FP64 oracle (oracle/) on paper_2306_07212_gb300.workloads.counting_sweep_net; "
                      "written by tests/golden/make_counting_sweep.py",
            "box": "[-1,1]^D", "network": "[D, w, w, w, w, 1], uniform +-1/sqrt(fan_in), rounded to FP32",
