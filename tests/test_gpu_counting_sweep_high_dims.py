@@ -1,8 +1,8 @@
 """The counting sweep of Section 5.1.2 at D = 5 and 6 on the GPU (the
 library takes D <= 8): identical complexes where the oracle finishes in
 under a second, and vertex and edge counts equal to the stored oracle counts
-at every stored point with D >= 5 (five nets each, up to 4.3e5 vertices and
-2e6 edges)."""
+at every stored point with D >= 5 (five nets each; the largest hold about
+1e7 to 2e7 vertices and 5e7 to 1e8 edges)."""
 import json
 import os
 
