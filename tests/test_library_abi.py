@@ -95,3 +95,32 @@ def test_header_is_plain_c_and_host_calls_work(lib_path, tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.strip().endswith("ok")
+
+
+def test_ctypes_structures_match_the_header(tmp_path):
+    """Every field of pc_options, pc_server_options and pc_result sits at the
+    same offset in the binding's ctypes structures as in the C header, and
+    the structures have the same size."""
+    import shutil
+    from paper_2306_07212_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path / "layout")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I" + os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "c", "layout.c"), "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    classes = {"pc_options": binding.Options, "pc_server_options": binding.ServerOptions,
+               "pc_result": binding.Result}
+    seen = {k: set() for k in classes}
+    for line in filter(None, out):
+        struct, field, value = line.split()
+        cls = classes[struct]
+        if field == "sizeof":
+            assert ctypes.sizeof(cls) == int(value), struct
+        else:
+            assert getattr(cls, field).offset == int(value), (struct, field)
+            seen[struct].add(field)
+    for struct, cls in classes.items():
+        assert seen[struct] == {f for f, _ in cls._fields_}, struct
