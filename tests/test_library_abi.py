@@ -124,3 +124,22 @@ def test_ctypes_structures_match_the_header(tmp_path):
             seen[struct].add(field)
     for struct, cls in classes.items():
         assert seen[struct] == {f for f, _ in cls._fields_}, struct
+
+
+def test_binding_argtypes_match_the_header_arity(lib_path):
+    """Every function of include/pc.h has ctypes argtypes in the binding with
+    as many parameters as the declaration."""
+    from paper_2306_07212_gb300 import binding
+    src = open(os.path.join(ROOT, "include", "pc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    decls = re.findall(r"\b(pc_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src)
+    lib = binding.load_library()
+    checked = 0
+    for name, params in decls:
+        params = " ".join(params.split())
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        argtypes = getattr(lib, name).argtypes
+        assert argtypes is not None, f"{name} has no argtypes in the binding"
+        assert len(argtypes) == n, (name, len(argtypes), n)
+        checked += 1
+    assert checked >= 30
