@@ -39,3 +39,9 @@ def test_missing_library_raises():
             "    print('raised', 'no CPU fallback' in str(e))\n") % ROOT
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert out.stdout.strip() == "raised True", out.stdout + out.stderr
+
+
+def test_oracle_includes_only_standard_headers():
+    src = open(os.path.join(ROOT, "oracle", "oracle.cpp")).read()
+    includes = [l.split()[1] for l in src.splitlines() if l.startswith("#include")]
+    assert includes and all(i.startswith("<") for i in includes), includes
