@@ -16,10 +16,11 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
 
 
-# GPU modules that run after all the others, in this order: the counting
-# sweep (sixty extractions up to 5e6 edges), the polyhedral domains, then the
-# counting sweep at D = 5 and 6
-_LAST = {"test_gpu_counting_sweep.py": 1, "test_gpu_domains.py": 2, "test_gpu_counting_sweep_high_dims.py": 3}
+# GPU modules that run after all the others, in this order: rejected inputs,
+# the counting sweep (sixty extractions up to 5e6 edges), the polyhedral
+# domains, then the counting sweep at D = 5 and 6
+_LAST = {"test_gpu_invalid_inputs.py": 1, "test_gpu_counting_sweep.py": 2, "test_gpu_domains.py": 3,
+         "test_gpu_counting_sweep_high_dims.py": 4}
 
 
 def pytest_collection_modifyitems(config, items):
