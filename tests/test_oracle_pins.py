@@ -59,6 +59,22 @@ def test_matches_brute_force_tiny_deep(D, widths, seed):
     assert_same_complex(_triple(r), _triple(b), coord_tol=1e-9, what=f"{widths} seed {seed}")
 
 
+HIGH = [(4, [4, 3, 2, 1]), (5, [5, 3, 1]), (5, [5, 2, 2, 1]), (6, [6, 3, 1]), (6, [6, 2, 2, 1]),
+        (7, [7, 2, 1]), (8, [8, 2, 1]), (8, [8, 2, 1, 1])]
+
+
+@pytest.mark.parametrize("D,widths", HIGH)
+@pytest.mark.parametrize("seed", [0, 1])
+def test_matches_brute_force_up_to_d8(D, widths, seed):
+    # the dimensions of the counting sweep that the library takes (D <= 8)
+    net = wl.he_normal_mlp(widths, seed=50 + seed)
+    box = wl.Box.cube(D)
+    r = oracle.extract(net, box)
+    b = oracle.brute(net, box, tol=1e-9)
+    assert r.status == 0 and b.status == 0, (r.error, b.error)
+    assert_same_complex(_triple(r), _triple(b), coord_tol=1e-9, what=f"{widths} seed {seed}")
+
+
 @pytest.mark.slow
 def test_small_d2_config_matches_brute_force():
     net, box = wl.small_d2()
