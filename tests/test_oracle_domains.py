@@ -89,3 +89,14 @@ def test_corner_cut_skeleton_and_euler_characteristic(D):
     r = oracle.extract_domain(wl.he_normal_mlp([D, 8, 8, 1], seed=D), dom)
     f, chi = oracle.faces(r)
     assert r.status == 0 and chi == 1
+
+
+@pytest.mark.parametrize("name", ["simplex", "corner_cut"])
+@pytest.mark.parametrize("widths", [[4, 3, 2, 1], [5, 3, 1], [6, 2, 2, 1]])
+def test_higher_dimensional_domains_match_brute_force(name, widths):
+    net = wl.he_normal_mlp(widths, seed=61)
+    dom = getattr(wl.Polytope, name)(widths[0])
+    r = oracle.extract_domain(net, dom)
+    b = oracle.brute_domain(net, dom, tol=1e-9)
+    assert r.status == 0 and b.status == 0, (r.error, b.error)
+    assert_same_complex((r.X, r.S, r.E), (b.X, b.S, b.E), coord_tol=1e-9, what=f"{name} {widths}")
