@@ -43,8 +43,8 @@ def _regions(W, b, A, c):
     return total
 
 
-@pytest.mark.parametrize("D,n", [(2, 6), (2, 15), (3, 5), (3, 9)])
-@pytest.mark.parametrize("domain", ["box", "simplex"])
+@pytest.mark.parametrize("D,n", [(2, 6), (2, 15), (3, 5), (3, 9), (4, 6), (5, 6)])
+@pytest.mark.parametrize("domain", ["box", "simplex", "corner_cut"])
 def test_regions_of_a_clipped_arrangement(D, n, domain):
     net = wl.he_normal_mlp([D, n], seed=10 * D + n, bias_var=0.25)
     if domain == "box":
@@ -52,7 +52,7 @@ def test_regions_of_a_clipped_arrangement(D, n, domain):
         dom = wl.Polytope.from_box(box)
         r = oracle.extract(net, box)
     else:
-        dom = wl.Polytope.simplex(D)
+        dom = getattr(wl.Polytope, domain)(D)
         r = oracle.extract_domain(net, dom)
     assert r.status == 0
     f, chi = oracle.faces(r)
