@@ -66,7 +66,8 @@ def test_pruned_is_a_subcomplex_with_the_same_level_set(D, widths, seed):
 
 
 @pytest.mark.parametrize("D,widths", [(2, [2, 4, 3, 1]), (2, [2, 3, 3, 3, 1]), (3, [3, 4, 3, 1]),
-                                      (3, [3, 3, 3, 3, 1])])
+                                      (3, [3, 3, 3, 3, 1]), (4, [4, 3, 2, 1]), (5, [5, 2, 2, 1]),
+                                      (6, [6, 2, 2, 1])])
 @pytest.mark.parametrize("seed", [0, 1, 2, 3])
 def test_pruned_level_set_matches_brute_force(D, widths, seed):
     net = wl.he_normal_mlp(widths, seed=200 + seed)
