@@ -17,7 +17,8 @@ extraction on the same workload (`variants`), the serving measurement (`serving`
 5.1.2 (`counting_sweep`: vertex and edge counts, time and peak device memory
 of random four-hidden-layer nets of widths 10, 20, 40 for D = 1..5, five nets
 per point; `--sweep-dims ''` skips it), the same net on a simplex domain
-(`domain`; `--domain 0` skips it), the roofline of the neuron loop, the
+(`domain`; `--domain 0` skips it), the width-10 sweep nets for D = 6..10
+(`counting_sweep_w10`; `--sweep-dims-w10 ''` skips it), the roofline of the neuron loop, the
 clocks seen during the timed region and one oracle run on a host core.
 
 --impl reference times the FP64 CPU oracle as the reference arm
@@ -321,6 +322,14 @@ def run_ours(args, rank, world, local_rank):
                 out["domain"] = run_domain(net, params_dev, flush, local_rank, args)
             except Exception as exc:
                 out["domain"] = {"error": str(exc)[:300]}
+        if args.sweep_dims_w10 and world == 1:
+            # the width-10 nets further up in D (D > 8 on the PC_MAX_D=10 build)
+            try:
+                out["counting_sweep_w10"] = run_counting_sweep(_dims(args.sweep_dims_w10), args.sweep_seeds,
+                                                               local_rank, args.precision, args.execution,
+                                                               widths=(10,))
+            except Exception as exc:
+                out["counting_sweep_w10"] = {"error": str(exc)[:300]}
     ex.close()
     if dist:
         dist.destroy_process_group()
@@ -390,21 +399,22 @@ def zero_residual(net, box, X, words) -> float:
     import numpy as np
     X = np.asarray(X, np.float64)
     words = np.asarray(words, np.uint64)
-    vals = [X - box.lo, box.hi - X]
-    facets = np.empty((len(X), 2 * net.D))
-    facets[:, 0::2], facets[:, 1::2] = vals
-    cols, a = [facets], X
-    for W, b in zip(net.W, net.b):
-        z = a @ W.T + b
-        cols.append(z)
-        a = np.maximum(z, 0.0)
-    allv = np.concatenate(cols, axis=1)
     worst = 0.0
-    for j in range(allv.shape[1]):
-        code = (words[j // 32] >> np.uint64(2 * (j % 32))) & np.uint64(3)
-        on = code == 0
-        if on.any():
-            worst = max(worst, float(np.abs(allv[on, j]).max()))
+    for r0 in range(0, len(X), 1 << 20):  # bounded host memory
+        x = X[r0:r0 + (1 << 20)]
+        w = words[:, r0:r0 + (1 << 20)]
+        facets = np.empty((len(x), 2 * net.D))
+        facets[:, 0::2], facets[:, 1::2] = x - box.lo, box.hi - x
+        cols, a = [facets], x
+        for W, b in zip(net.W, net.b):
+            z = a @ W.T + b
+            cols.append(z)
+            a = np.maximum(z, 0.0)
+        allv = np.concatenate(cols, axis=1)
+        for j in range(allv.shape[1]):
+            on = ((w[j // 32] >> np.uint64(2 * (j % 32))) & np.uint64(3)) == 0
+            if on.any():
+                worst = max(worst, float(np.abs(allv[on, j]).max()))
     return worst / float(np.max(box.hi - box.lo))
 
 
@@ -417,15 +427,16 @@ def _dims(spec: str) -> list:
     return sorted(dims)
 
 
-def run_counting_sweep(dims, seeds: int, device: int, precision: str, execution: str):
+def run_counting_sweep(dims, seeds: int, device: int, precision: str, execution: str, widths=None):
     """Counting sweep (Section 5.1.2): per input dimension D and width w, nets
     of four hidden layers of w on [-1,1]^D, `seeds` random nets each; vertex
     and edge counts, extraction time and peak device memory, mean and standard
     deviation over the nets.  Each net gets a fresh context: `cold_ms` is its
     first extraction (capacity growth included), `ms` the median of three more,
     `peak_mib` the most device memory allocated above what was held before;
-    at width 10 (the paper's validation nets) `zero_residual_rel` is the
-    largest zero-entry residual over the nets (zero_residual)."""
+    at width 10 `zero_residual_rel` is the largest zero-entry residual of
+    the first net (zero_residual; the paper validates one fixed 4-layer
+    width-10 net per dimension)."""
     import numpy as np
     import torch
     from paper_2306_07212_gb300 import Extractor, workloads
@@ -443,7 +454,8 @@ def run_counting_sweep(dims, seeds: int, device: int, precision: str, execution:
 
     t_start = time.perf_counter()
     points = []
-    for width in workloads.COUNTING_WIDTHS:
+    widths = tuple(widths or workloads.COUNTING_WIDTHS)
+    for width in widths:
         for D in dims:
             rows, residual = [], 0.0
             try:
@@ -453,13 +465,14 @@ def run_counting_sweep(dims, seeds: int, device: int, precision: str, execution:
                     torch.cuda.synchronize()
                     base = torch.cuda.memory_allocated(device)
                     torch.cuda.reset_peak_memory_stats(device)
-                    with Extractor(device=device, precision=precision, execution=execution) as ex:
+                    with Extractor(device=device, precision=precision, execution=execution,
+                                   max_dim=8 if D <= 8 else 10) as ex:
                         cold = timed(ex, net, box, params)
                         peak = torch.cuda.max_memory_allocated(device) - base
                         warm = statistics.median([timed(ex, net, box, params) for _ in range(3)])
                         c = ex.counts()
-                        if width == 10:  # the paper's validation net: four layers of width 10
-                            residual = max(residual, zero_residual(net, box, ex.vertices(), ex.sign_words()))
+                        if width == 10 and seed == 0:  # the paper validates one fixed 4-layer width-10 net
+                            residual = zero_residual(net, box, ex.vertices(), ex.sign_words())
                     rows.append((c["nV"], c["nE"], cold, warm, peak / 2**20))
             except Exception as exc:  # e.g. a dimension the library does not take
                 points.append({"D": D, "width": width, "error": str(exc)[:200]})
@@ -471,7 +484,7 @@ def run_counting_sweep(dims, seeds: int, device: int, precision: str, execution:
             if width == 10:
                 points[-1]["zero_residual_rel"] = float(f"{residual:.3g}")
     return {"workload": f"Section 5.1.2 counting sweep: MLP [D, w, w, w, w, 1], w in "
-                        f"{list(workloads.COUNTING_WIDTHS)}, D in {dims}, {seeds} uniformly initialised nets per "
+                        f"{list(widths)}, D in {dims}, {seeds} uniformly initialised nets per "
                         f"point (FP32 weights), box [-1,1]^D, {precision} precision; values are [mean, std]",
             "points": points, "seconds": round(time.perf_counter() - t_start, 1)}
 
@@ -540,6 +553,8 @@ def main():
     ap.add_argument("--sweep-dims", default="1-5",
                     help="input dimensions of the counting sweep, e.g. 1-4 or 1,2,5 ('' = skip it)")
     ap.add_argument("--sweep-seeds", type=int, default=5, help="random nets per counting-sweep point")
+    ap.add_argument("--sweep-dims-w10", default="6-10",
+                    help="input dimensions of the width-10 counting sweep beyond --sweep-dims ('' = skip it)")
     ap.add_argument("--domain", type=int, default=1, help="1: also time the net on a simplex domain")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))

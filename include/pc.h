@@ -153,7 +153,8 @@ pc_status pc_set_allocator(pc_ctx *ctx, pc_alloc_fn alloc, pc_free_fn free_fn, v
  * parameters (layout above), host or device memory.  box_lo/box_hi: host
  * arrays of D doubles.  stream: cudaStream_t (NULL = legacy default stream).
  * Blocks until the result is ready (one device->host status read).
- * Limits: 1 <= D <= 8, widths <= 256, 2D + sum(widths[1..L]) <= 1024.
+ * Limits: 1 <= D <= 8 (D <= 10 in libpc_d10.so, the same sources built with
+ * PC_MAX_D=10), widths <= 256, 2D + sum(widths[1..L]) <= 1024.
  * Returns PC_ERR_PAIRING / PC_ERR_DEGENERATE (strict) when genericity fails. */
 pc_status pc_extract(pc_ctx *ctx, int L, const int32_t *widths, const double *params,
                      const double *box_lo, const double *box_hi, void *stream);

@@ -14,7 +14,7 @@ from typing import Optional
 
 import numpy as np
 
-from .buildlib import LIB
+from .buildlib import LIB, LIB_D10
 
 PC_OK = 0
 STATUS_NAMES = {0: "PC_OK", 1: "PC_ERR_INVALID", 2: "PC_ERR_OOM", 3: "PC_ERR_CUDA",
@@ -64,16 +64,16 @@ class Options(ctypes.Structure):
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
-_lib = None
+_libs = {}
 _lock = threading.Lock()
 
 
 def load_library(path: str = LIB):
-    """Loads libpc.so; raises if it has not been built."""
-    global _lib
+    """Loads libpc.so (or another build of it, e.g. LIB_D10); raises if it
+    has not been built."""
     with _lock:
-        if _lib is not None:
-            return _lib
+        if path in _libs:
+            return _libs[path]
         if not os.path.exists(path):
             raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
                                "(there is no CPU fallback)")
@@ -121,7 +121,7 @@ def load_library(path: str = LIB):
             if f not in ("pc_default_options", "pc_last_error", "pc_estimate_bytes", "pc_server_default_options",
                          "pc_server_error"):
                 getattr(lib, f).restype = ctypes.c_int
-        _lib = lib
+        _libs[path] = lib
         return lib
 
 
@@ -169,14 +169,18 @@ class Extractor:
     precision: "fp32" | "mixed" (FP32 bulk, FP64 re-evaluation of signs within
     the FP32 error bound) | "fp64".  execution: "persistent" (one cooperative
     kernel per layer) | "stepwise" (one kernel per step and neuron).
+    max_dim: the largest input dimension the context takes, 8 (libpc.so) or
+    10 (libpc_d10.so, the same kernels with larger per-vertex arrays).
     """
 
     def __init__(self, device: int = 0, precision: str = "mixed", execution: str = "persistent",
                  keep_tape: bool = False, strict: bool = False, init_vcap: int = 0, init_ecap: int = 0,
                  mem_budget_bytes: int = 0, kappa: float = 12.0, polish: int = -1, polish_tol: float = 1e-6,
                  timers: bool = False, torch_allocator: bool = True, gemm: str = "tensor",
-                 pairing: str = "deferred", canonical: bool = False, prune: bool = False):
-        self._lib = load_library()
+                 pairing: str = "deferred", canonical: bool = False, prune: bool = False, max_dim: int = 8):
+        if not 1 <= max_dim <= 10:
+            raise ValueError("max_dim must be in [1, 10]")
+        self._lib = load_library(LIB if max_dim <= 8 else LIB_D10)
         o = Options()
         self._lib.pc_default_options(ctypes.byref(o))
         o.precision = PRECISION[precision]

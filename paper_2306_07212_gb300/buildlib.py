@@ -1,8 +1,10 @@
 """Builds libpc.so (all CUDA sources under csrc/) in-tree for sm_103a.
 
 Each translation unit is compiled by its own nvcc process (in parallel), then
-linked into ``_build/libpc.so``.  Rebuilds only when a source or header is
-newer than the library.
+linked into ``_build/libpc.so``.  The same sources compiled with
+-DPC_MAX_D=10 link into ``_build/libpc_d10.so``, the build for input
+dimensions 9 and 10 (libpc.so takes D <= 8).  Rebuilds only when a source or
+header is newer than a library.
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpc.so")
+LIB_D10 = os.path.join(BUILD, "libpc_d10.so")
+VARIANTS = {LIB: [], LIB_D10: ["-DPC_MAX_D=10"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
@@ -33,15 +37,20 @@ def _deps():
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not all(os.path.exists(lib) for lib in VARIANTS):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(lib) for lib in VARIANTS)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [NVCC] + ARCH + FLAGS + ["-c", src, "-o", obj]
+def _objdir(lib: str) -> str:
+    return BUILD if lib == LIB else os.path.join(BUILD, os.path.basename(lib)[:-3])
+
+
+def _compile(src: str, lib: str, verbose: bool) -> str:
+    os.makedirs(_objdir(lib), exist_ok=True)
+    obj = os.path.join(_objdir(lib), os.path.basename(src)[:-3] + ".o")
+    cmd = [NVCC] + ARCH + FLAGS + VARIANTS[lib] + ["-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -57,14 +66,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    jobs = [(src, lib) for lib in VARIANTS for src in srcs]
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
+        objs = list(ex.map(lambda j: _compile(j[0], j[1], verbose), jobs))
+    for lib in VARIANTS:
+        tmp = lib + f".tmp{os.getpid()}"
+        mine = [o for o, (_, l) in zip(objs, jobs) if l == lib]
+        cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + mine + ["-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -714,7 +714,7 @@ struct DomainIn {
 // twice, D edges at every vertex; a full-dimensional bounding box.  Returns
 // "" or the reason; on success lo / hi receive the bounding box.
 static std::string check_domain(int D, const DomainIn& d, double* lo, double* hi) {
-  if (D < 1 || D > kMaxD) return "input dimension must be in [1, 8]";
+  if (D < 1 || D > kMaxD) return "input dimension must be in [1, " + std::to_string(kMaxD) + "]";
   if (d.m < D + 1 || d.m > kMaxEntries) return "the number of facets must be in [D + 1, 1024]";
   if (!d.A || !d.c || !d.X0 || !d.E0) return "null domain array";
   if (d.nv0 < D + 1 || d.nv0 > (1ll << 20)) return "the skeleton needs D + 1 to 2^20 vertices";
@@ -780,7 +780,8 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   c->deferred = deferred ? 1 : 0;
   if (L < 1 || L > kMaxL) throw PcError(PC_ERR_INVALID, "number of layers must be in [1, 16]");
   const int D = widths[0];
-  if (D < 1 || D > kMaxD) throw PcError(PC_ERR_INVALID, "input dimension must be in [1, 8]");
+  if (D < 1 || D > kMaxD)
+    throw PcError(PC_ERR_INVALID, "input dimension must be in [1, " + std::to_string(kMaxD) + "]");
   NetDesc& net = c->net;
   net = NetDesc{};
   net.L = L;

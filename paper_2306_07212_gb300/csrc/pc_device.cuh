@@ -22,7 +22,13 @@
 
 namespace pc {
 
-constexpr int kMaxD = 8;
+// Largest input dimension: 8 in libpc.so; the same sources compiled with
+// -DPC_MAX_D=10 give libpc_d10.so for D = 9, 10 (its per-vertex Newton
+// arrays and shared-memory tiles are sized by it).
+#ifndef PC_MAX_D
+#define PC_MAX_D 8
+#endif
+constexpr int kMaxD = PC_MAX_D;
 constexpr int kMaxL = 16;
 constexpr int kMaxWidth = 256;
 constexpr int kMaxEntries = 1024;

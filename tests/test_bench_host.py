@@ -32,8 +32,9 @@ class _Event:
 class _FakeExtractor:
     opened = []
 
-    def __init__(self, device, precision, execution):
+    def __init__(self, device, precision, execution, max_dim=8):
         self.args = (device, precision, execution)
+        self.max_dim = max_dim
         _FakeExtractor.opened.append(self)
         self.closed = False
 
@@ -44,8 +45,8 @@ class _FakeExtractor:
         self.closed = True
 
     def extract(self, net, box, params=None):
-        if net.D > 8:
-            raise RuntimeError("input dimension must be in [1, 8]")
+        if net.D > self.max_dim:
+            raise RuntimeError(f"input dimension must be in [1, {self.max_dim}]")
         self.net = net
 
     def counts(self):
@@ -99,11 +100,19 @@ def test_counting_sweep_points_and_statistics(faked):
 
 
 def test_counting_sweep_records_a_failing_point(faked):
-    out = bench.run_counting_sweep([8, 9], seeds=1, device=0, precision="mixed", execution="persistent")
+    out = bench.run_counting_sweep([8, 11], seeds=1, device=0, precision="mixed", execution="persistent")
     by = {(p["D"], p["width"]): p for p in out["points"]}
-    assert "error" in by[(9, 10)] and "[1, 8]" in by[(9, 10)]["error"]
+    assert "error" in by[(11, 10)] and "[1, 10]" in by[(11, 10)]["error"]
     assert "error" not in by[(8, 40)] and by[(8, 40)]["nV"][0] == 840.0
     assert len(out["points"]) == 6 and np.isfinite(out["seconds"])
+
+
+def test_width_10_sweep_uses_the_d10_build_above_8(faked):
+    out = bench.run_counting_sweep([7, 9, 10], seeds=1, device=0, precision="mixed", execution="persistent",
+                                   widths=(10,))
+    assert [(p["D"], p["width"]) for p in out["points"]] == [(7, 10), (9, 10), (10, 10)]
+    assert [e.max_dim for e in _FakeExtractor.opened] == [8, 10, 10]
+    assert all("error" not in p and "zero_residual_rel" in p for p in out["points"])
 
 
 def test_host_cpu_reports_cores():
@@ -150,3 +159,16 @@ def test_zero_residual_of_an_exact_complex_and_a_shifted_one():
     X = r.X.copy()
     X[5] += 1e-4  # one vertex moved off its zero set
     assert 1e-6 < bench.zero_residual(net, box, X, words) < 1e-3
+
+
+def test_zero_residual_sees_every_chunk():
+    import oracle
+    from paper_2306_07212_gb300 import workloads as wl
+    net, box = wl.counting_sweep_net(2, 10, seed=2)
+    r = oracle.extract(net, box)
+    reps = (1 << 20) // r.nV + 2  # more rows than one chunk
+    X = np.tile(r.X, (reps, 1))
+    words = np.tile(_pack(r.S), (1, reps))
+    assert bench.zero_residual(net, box, X, words) < 1e-13
+    X[-1] += 1e-4  # a vertex in the last chunk moved off its zero set
+    assert bench.zero_residual(net, box, X, words) > 1e-6

@@ -26,13 +26,15 @@ def lib_path():
     return buildlib.build()
 
 
-def test_library_exports_every_declared_symbol(lib_path):
+@pytest.mark.parametrize("variant", ["libpc.so", "libpc_d10.so"])
+def test_library_exports_every_declared_symbol(lib_path, variant):
     declared = _declared()
     assert {"pc_create", "pc_extract", "pc_vertices", "pc_edges", "pc_signvectors", "pc_backward"} <= declared
-    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    path = os.path.join(os.path.dirname(lib_path), variant)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
     exported = set(re.findall(r"\bT (pc_[a-z_0-9]+)\b", out))
     assert declared <= exported, f"missing: {declared - exported}"
-    lib = ctypes.CDLL(lib_path)
+    lib = ctypes.CDLL(path)
     for name in declared:
         assert getattr(lib, name)
 
