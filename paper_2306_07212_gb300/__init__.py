@@ -17,8 +17,11 @@ Typical use::
 Options of ``Extractor``: ``execution`` ("persistent" | "stepwise"),
 ``canonical`` (fixed output order), ``prune`` (level-set extraction),
 ``keep_tape`` (for ``backward`` / ``autograd.extract_vertices``), ``gemm``
-("tensor" | "simt" | "tensor3x"), ``pairing`` ("deferred" | "inline").
-``binding.Server`` serves many requests concurrently on one GPU.
+("tensor" | "simt" | "tensor3x"), ``pairing`` ("deferred" | "inline"),
+``max_dim`` (8, or 10 for the build that takes D = 9, 10).
+``Extractor.extract_domain`` takes a polyhedral domain (``workloads.Polytope``)
+instead of a box; ``binding.Server`` serves many requests concurrently on
+one GPU.
 """
 from .binding import Extractor, PcError, load_library  # noqa: F401
 from . import workloads  # noqa: F401
