@@ -129,6 +129,13 @@ typedef struct {
                              the vertices without an edge; the result keeps
                              the output neuron's zero set and its
                              neighbourhood.  Not with keep_tape */
+  int debug_barrier_timeout; /* testing only (0 in normal use): 1 makes every
+                             grid barrier of the persistent kernel wait for one
+                             arrival more than the grid has, with a spin limit
+                             of 4096 polls, so that the wait runs out and the
+                             extraction returns PC_ERR_TIMEOUT; exercises the
+                             bounded-wait error path without hanging the GPU.
+                             No effect in PC_EXEC_STEPWISE (no grid barrier) */
 } pc_options;
 
 /* Fills *opt with defaults (mixed precision, persistent execution,
@@ -247,7 +254,11 @@ pc_status pc_cell_counts(pc_ctx *ctx, int64_t *f_out, int n, int64_t *euler);
  * (cumulative over the context's life), capacity growths, polished vertices,
  * exact-zero pre-activations, FP64-undecidable signs, vertex / edge / hash
  * capacities, device bytes held, CTAs of the persistent kernel, extractions
- * repeated with inline pairing after a failed fingerprint check (cumulative). */
+ * repeated with inline pairing after a failed fingerprint check (cumulative),
+ * FP64 re-decisions that changed the FP32 sign (PC_PREC_MIXED), and the
+ * largest |z| / (FP32 error estimate of z) among those, times 1000 and
+ * rounded up (the filter re-decides every |z| <= filter_kappa x estimate, so
+ * a margin near filter_kappa means a flip close to the filter's edge). */
 pc_status pc_diagnostics(pc_ctx *ctx, int64_t *out, int n);
 
 /* With opt.timers: device time in ms of the last extraction's kernels,
@@ -333,12 +344,19 @@ pc_status pc_server_destroy(pc_server *s);
  * uint64, S = (2D + neurons + 31) / 32); *n_vertices / *n_edges (host).
  * Blocks until done.
  *
+ * Alignment: cap_e must be a multiple of 4 and E must start on a 16-byte
+ * boundary (the edge pass reads both endpoint rows with 16-byte loads); X
+ * and SIG must be 8-byte aligned.  Otherwise the call returns PC_ERR_INVALID
+ * before any device work.
+ *
  * All other working memory is one static device array of about 10.6 MB
  * inside the library, held on every GPU that loads it until the process
  * exits.  Limits: cap_v <= 16384, cap_e <= 65536, layer widths <= 32, at most
  * 512 neurons and 16384 parameters; beyond them the call returns
  * PC_ERR_TOO_LARGE, and an extraction that outgrows the capacities returns
- * PC_ERR_OOM (nothing grows).  The call allocates nothing: no cudaMalloc,
+ * PC_ERR_OOM (nothing grows; the next call starts afresh).  Step (5) pairs
+ * every 2-face with a full sign-vector comparison before it pairs (the
+ * inline form of pc_pairing), so no check after the extraction is needed.  The call allocates nothing: no cudaMalloc,
  * cudaFree or allocating library routine.  The first call on a device looks
  * up the scratch array's device address (cudaGetSymbolAddress) with that
  * device current; make that first call before any stream capture.  Every

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -111,7 +112,7 @@ __global__ void k_init(NetDesc net, State st) {
     st.cnt[0] = c0;
     Global g{};
     g.halted_at = -1;
-    g.flip_at = -1;
+    g.barrier_extra = net.debug_barrier ? 1u : 0u;
     *st.g = g;
   }
 }
@@ -157,7 +158,7 @@ __global__ void k_init_domain(NetDesc net, State st, const double* X0, const int
     st.cnt[0] = c0;
     Global g{};
     g.halted_at = -1;
-    g.flip_at = -1;
+    g.barrier_extra = net.debug_barrier ? 1u : 0u;
     *st.g = g;
   }
 }
@@ -262,50 +263,60 @@ __global__ void __launch_bounds__(128) k_gemm_simt(NetDesc net, State st, int l)
 // ---------------------------------------------------------------------------
 // Neuron phases: stepwise kernels and the persistent per-layer kernel.
 
-
 template <typename ZT, bool MIXED>
-__global__ void __launch_bounds__(kBlock, 2) k_classify(NetDesc net, State st, int l, int i, int mw) {
+__global__ void __launch_bounds__(kBlock, 2) k_decide(NetDesc net, State st, int l, int mw) {
   extern __shared__ double dsm[];
   __shared__ Smem sm;
   if (cta_stopped(st)) return;
-  phase_classify<ZT, MIXED>(net, st, l, l, i, net.off[l] + i, sm, dsm, mw);
+  phase_decide<ZT, MIXED>(net, st, l, sm, dsm, mw);
 }
 
-__global__ void __launch_bounds__(kBlock) k_reclassify(NetDesc net, State st, int l, int i) {
-  __shared__ Smem sm;
+template <typename ZT>
+__global__ void __launch_bounds__(kBlock) k_scan0(NetDesc net, State st, int l) {
   if (cta_stopped(st)) return;
-  const int n = net.off[l] + i;
-  if (*(volatile int*)&st.g->flip_at != n) return;  // written by the previous launch only
-  phase_reclassify(net, st, n, sm);
+  phase_scan0<ZT>(net, st, l);
 }
 
 template <typename ZT, bool MIXED>
-__global__ void __launch_bounds__(kBlock, 2) k_split(NetDesc net, State st, int l, int i) {
+__global__ void __launch_bounds__(kBlock, 2) k_step(NetDesc net, State st, int l, int i, int mw) {
+  extern __shared__ double dsm[];
   __shared__ Smem sm;
   if (cta_stopped(st)) return;
-  phase_split<ZT, MIXED>(net, st, l, l, i, net.off[l] + i, sm);
+  phase_step<ZT, MIXED>(net, st, l, i, sm, dsm, mw);
 }
 
+template <typename ZT>
+__global__ void __launch_bounds__(kBlock) k_pack(NetDesc net, State st, int l) {
+  if (cta_stopped(st)) return;
+  phase_pack<ZT>(net, st, l);
+}
+
+// The neuron loop of layer l in one cooperative launch: the layer-start
+// decisions and first edge scan (prologue = 1; a launch that resumes after a
+// capacity halt skips them), one grid barrier per neuron step, and the
+// packing of the layer's sign codes.
 template <typename ZT, bool MIXED>
-__global__ void __launch_bounds__(kBlock, 2) k_layer(NetDesc net, State st, int l, int i_begin, int mw) {
+__global__ void __launch_bounds__(kBlock, 2) k_layer(NetDesc net, State st, int l, int i_begin, int prologue,
+                                                     int mw) {
   extern __shared__ double dsm[];
   __shared__ Smem sm;
   if (cta_stopped(st)) return;
   unsigned int passed = 0;
   const int H = net.w[l + 1];
-  for (int i = i_begin; i < H; ++i) {
-    const int n = net.off[l] + i;
-    phase_classify<ZT, MIXED>(net, st, l, l, i, n, sm, dsm, mw);
+  if (prologue) {
+    phase_decide<ZT, MIXED>(net, st, l, sm, dsm, mw);
     if (!grid_barrier(st.g, passed)) return;  // uniform per CTA
     if (cta_stopped(st)) return;
-    if (MIXED && *(volatile int*)&st.g->flip_at == n) {
-      phase_reclassify(net, st, n, sm);
-      if (!grid_barrier(st.g, passed)) return;
-    }
-    if (phase_split<ZT, MIXED>(net, st, l, l, i, n, sm)) return;
+    phase_scan0<ZT>(net, st, l);
     if (!grid_barrier(st.g, passed)) return;
     if (cta_stopped(st)) return;
   }
+  for (int i = i_begin; i < H; ++i) {
+    if (phase_step<ZT, MIXED>(net, st, l, i, sm, dsm, mw)) return;
+    if (!grid_barrier(st.g, passed)) return;
+    if (cta_stopped(st)) return;
+  }
+  phase_pack<ZT>(net, st, l);
 }
 
 // Exact check of every pairing made by fingerprint (deferred mode), after
@@ -480,14 +491,17 @@ static void realloc_state(pc_ctx* c, long long V, long long E, long long T, bool
   A(nb.exc, sizeof(float) * V);
   A(nb.SIG, sizeof(uint64_t) * S * V);
   A(nb.E, sizeof(int32_t) * 2 * E);
-  A(nb.stage, sizeof(int4) * E);
+  A(nb.list0, sizeof(int4) * E);
+  A(nb.list1, sizeof(int4) * E);
+  A(nb.flags, sizeof(uint32_t) * 2 * (E / 32));
   A(nb.vlist, sizeof(int4) * E);
-  A(nb.table, 16 * T);
+  A(nb.table, 32 * T);
   if (c->opt.keep_tape) {
     A(nb.tape_pq, sizeof(int32_t) * 2 * V);
     A(nb.tape_t, sizeof(double) * V);
   }
-  PC_CUDA(cudaMemsetAsync(nb.table, 0xff, 16 * T, c->stream));
+  PC_CUDA(cudaMemsetAsync(nb.table, 0xff, 32 * T, c->stream));
+  PC_CUDA(cudaMemsetAsync(nb.flags, 0, sizeof(uint32_t) * 2 * (E / 32), c->stream));
   StateBufs& ob = c->bufs;
   if (copy && ob.X) {
     const long long oV = c->Vcap, oE = c->Ecap, nV = std::min(oV, V), nE = std::min(oE, E);
@@ -501,6 +515,10 @@ static void realloc_state(pc_ctx* c, long long V, long long E, long long T, bool
     cp2(nb.SIG, 8 * V, ob.SIG, 8 * oV, 8 * nV, S);
     cp2(nb.E, 4 * E, ob.E, 4 * oE, 4 * nE, 2);
     cp2(nb.vlist, 16 * E, ob.vlist, 16 * oE, 16 * nE, 1);
+    // the splitting edges (and their flags) of the step that resumes
+    cp2(nb.list0, 16 * E, ob.list0, 16 * oE, 16 * nE, 1);
+    cp2(nb.list1, 16 * E, ob.list1, 16 * oE, 16 * nE, 1);
+    cp2(nb.flags, 4 * (E / 32), ob.flags, 4 * (oE / 32), 4 * (nE / 32), 2);
     if (c->opt.keep_tape && ob.tape_pq) {
       cp2(nb.tape_pq, 4 * V, ob.tape_pq, 4 * oV, 4 * nV, 2);
       cp2(nb.tape_t, 8 * V, ob.tape_t, 8 * oV, 8 * nV, 1);
@@ -531,17 +549,10 @@ static void ensure_fixed(pc_ctx* c, int N) {
     }
     c->cnt_slots = N + 1;
   }
-  if (!c->g || !c->cta || !c->h_g) {
+  if (!c->g || !c->h_g) {
     ctx_free(c, c->g);
-    ctx_free(c, c->cta);
     c->g = ctx_alloc(c, sizeof(Global));
-    c->cta = ctx_alloc(c, sizeof(long long) * 2 * kMaxGrid);  // counts, then their step tags
-    if (!c->g || !c->cta) {
-      ctx_free(c, c->g);
-      ctx_free(c, c->cta);
-      throw PcError(PC_ERR_OOM, "status allocation failed");
-    }
-    PC_CUDA(cudaMemsetAsync(c->cta, 0, sizeof(long long) * 2 * kMaxGrid, c->stream));
+    if (!c->g) throw PcError(PC_ERR_OOM, "status allocation failed");
     if (!c->h_g && cudaMallocHost(&c->h_g, sizeof(Global)) != cudaSuccess) {
       cudaGetLastError();
       c->h_g = nullptr;
@@ -566,13 +577,15 @@ static State make_state(pc_ctx* c) {
   s.SIG = static_cast<uint64_t*>(c->bufs.SIG);
   s.EU = static_cast<int32_t*>(c->bufs.E);
   s.EW = s.EU + c->Ecap;
-  s.stage = static_cast<int4*>(c->bufs.stage);
+  s.list[0] = static_cast<int4*>(c->bufs.list0);
+  s.list[1] = static_cast<int4*>(c->bufs.list1);
+  s.flags[0] = static_cast<uint32_t*>(c->bufs.flags);
+  s.flags[1] = s.flags[0] + (c->Ecap + 31) / 32;
   s.table = static_cast<uint64_t*>(c->bufs.table);
   s.vlist = static_cast<int4*>(c->bufs.vlist);
   s.deferred = c->deferred;
   s.cnt = static_cast<Counters*>(c->cnt);
   s.g = static_cast<Global*>(c->g);
-  s.cta_count = static_cast<long long*>(c->cta);
   s.tape_pq = static_cast<int32_t*>(c->bufs.tape_pq);
   s.tape_t = static_cast<double*>(c->bufs.tape_t);
   s.tape_cap = c->opt.keep_tape ? c->Vcap : 0;
@@ -618,7 +631,9 @@ struct Kernels {
     PC_CUDA(cudaGetLastError());
     c->launches += 1;
   }
-  static void layer(pc_ctx* c, const State& st, int l, int i_begin) {
+  // The neuron loop of layer l from neuron i_begin; prologue: the layer's
+  // start (decisions, first edge scan) has not run yet.
+  static void layer(pc_ctx* c, const State& st, int l, int i_begin, bool prologue) {
     TimerScope ts(c, 2 * l + 1);
     const int H = c->net.w[l + 1];
     if (c->opt.exec == PC_EXEC_PERSISTENT) {
@@ -626,25 +641,27 @@ struct Kernels {
       auto fn = k_layer<ZT, MIXED>;
       NetDesc net = c->net;
       State s = st;
-      int l_ = l, ib = i_begin, mw = c->mw;
-      void* args[] = {&net, &s, &l_, &ib, &mw};
+      int l_ = l, ib = i_begin, pro = prologue ? 1 : 0, mw = c->mw;
+      void* args[] = {&net, &s, &l_, &ib, &pro, &mw};
       PC_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(c->grid_persist), dim3(kBlock), args,
                                           c->res_smem, c->stream));
       c->launches += 1;
     } else {
-      for (int i = i_begin; i < H; ++i) {
-        k_classify<ZT, MIXED><<<c->grid_step, kBlock, c->res_smem, c->stream>>>(c->net, st, l, i, c->mw);
+      if (prologue) {
+        k_decide<ZT, MIXED><<<c->grid_step, kBlock, c->res_smem, c->stream>>>(c->net, st, l, c->mw);
         PC_CUDA(cudaGetLastError());
-        c->launches += 1;
-        if (MIXED) {
-          k_reclassify<<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l, i);
-          PC_CUDA(cudaGetLastError());
-          c->launches += 1;
-        }
-        k_split<ZT, MIXED><<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l, i);
+        k_scan0<ZT><<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l);
+        PC_CUDA(cudaGetLastError());
+        c->launches += 2;
+      }
+      for (int i = i_begin; i < H; ++i) {
+        k_step<ZT, MIXED><<<c->grid_step, kBlock, c->res_smem, c->stream>>>(c->net, st, l, i, c->mw);
         PC_CUDA(cudaGetLastError());
         c->launches += 1;
       }
+      k_pack<ZT><<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l);
+      PC_CUDA(cudaGetLastError());
+      c->launches += 1;
     }
   }
   static int occupancy(pc_ctx* c) {
@@ -659,7 +676,7 @@ static void enqueue(pc_ctx* c, int l0, int i0, bool gemm_done) {
   const State st = make_state(c);
   for (int l = l0; l < c->net.L; ++l) {
     if (!(l == l0 && gemm_done)) Kernels<ZT, MIXED>::gemm(c, st, l);
-    Kernels<ZT, MIXED>::layer(c, st, l, l == l0 ? i0 : 0);
+    Kernels<ZT, MIXED>::layer(c, st, l, l == l0 ? i0 : 0, !(l == l0 && gemm_done));
     if (c->opt.prune && l + 1 < c->net.L) pc_prune_edges(c, st, l);
   }
 }
@@ -789,6 +806,7 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   net.m = dom ? dom->m : 2 * D;
   net.precision = c->opt.precision;
   net.kappa = static_cast<float>(c->opt.filter_kappa > 0 ? c->opt.filter_kappa : 2.0);
+  net.debug_barrier = c->opt.debug_barrier_timeout ? 1 : 0;
   long long p = 0;
   int n = 0, hmax = 0, mw = D;
   for (int l = 0; l <= L; ++l) {
@@ -891,7 +909,9 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     c->shape_nz = L;
     realloc_state(c, V, E, T, false);
   } else {
-    PC_CUDA(cudaMemsetAsync(c->bufs.table, 0xff, 16 * c->Tcap, c->stream));
+    // an earlier extraction that stopped early may have left keys and flags
+    PC_CUDA(cudaMemsetAsync(c->bufs.table, 0xff, 32 * c->Tcap, c->stream));
+    PC_CUDA(cudaMemsetAsync(c->bufs.flags, 0, sizeof(uint32_t) * 2 * (c->Ecap / 32), c->stream));
   }
   if (dom && (c->Vcap < dom->nv0 || c->Ecap < dom->ne0))
     realloc_state(c, std::max(c->Vcap, dom->nv0), std::max(c->Ecap, dom->ne0), c->Tcap, false);
@@ -935,14 +955,15 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     if (g.halt_reason & kHaltT) T = std::max(2 * T, pow2_at_least(g.need_t));
     V = std::min<long long>(V, (1ll << 31) - 1);
     E = std::min<long long>(E, (1ll << 31) - 1);
+    // the halted step wrote nothing: its list of splitting edges (copied with
+    // the buffers) and its counters carry over
     realloc_state(c, V, E, T, true);
-    // the neuron's counters restart from zero; the previous neuron used no table
-    PC_CUDA(cudaMemsetAsync(static_cast<Counters*>(c->cnt) + hn + 1, 0, sizeof(Counters), c->stream));
-    PC_CUDA(cudaMemsetAsync(&static_cast<Counters*>(c->cnt)[hn].tsize, 0, sizeof(long long), c->stream));
     Global g0{};
     g0.halted_at = -1;
-    g0.flip_at = -1;
     g0.error = g.error;
+    g0.flips = g.flips;
+    g0.flip_margin_bits = g.flip_margin_bits;
+    g0.barrier_extra = net.debug_barrier ? 1u : 0u;
     *static_cast<Global*>(c->h_g) = g0;
     PC_CUDA(cudaMemcpyAsync(c->g, c->h_g, sizeof(Global), cudaMemcpyHostToDevice, c->stream));
     l0 = hl;
@@ -976,6 +997,13 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   PC_CUDA(cudaMemcpyAsync(c->h_cnt, c->cnt, sizeof(Counters) * (n + 1), cudaMemcpyDeviceToHost, c->stream));
   PC_CUDA(cudaStreamSynchronize(c->stream));
   c->polished = static_cast<Global*>(c->h_g)->polished;
+  c->flips = static_cast<Global*>(c->h_g)->flips;
+  {
+    const int bits = static_cast<Global*>(c->h_g)->flip_margin_bits;
+    float f = 0.f;
+    std::memcpy(&f, &bits, sizeof(f));
+    c->flip_margin = f;
+  }
   for (int k = 0; k <= pc_ctx::kPolishSlot; ++k) {
     c->ktime_ms[k] = -1.0;
     if (c->ev_used[k]) {
@@ -1029,7 +1057,9 @@ void StateBufs::release(pc_ctx* c) {
   ctx_free(c, exc);
   ctx_free(c, SIG);
   ctx_free(c, E);
-  ctx_free(c, stage);
+  ctx_free(c, list0);
+  ctx_free(c, list1);
+  ctx_free(c, flags);
   ctx_free(c, vlist);
   ctx_free(c, table);
   ctx_free(c, tape_pq);
@@ -1048,9 +1078,12 @@ static cudaError_t set_func_attributes_now() {
   set((const void*)k_layer<double, false>, kNewtonSmemMax);
   set((const void*)k_layer<float, false>, kNewtonSmemMax);
   set((const void*)k_layer<float, true>, kNewtonSmemMax);
-  set((const void*)k_classify<double, false>, kNewtonSmemMax);
-  set((const void*)k_classify<float, false>, kNewtonSmemMax);
-  set((const void*)k_classify<float, true>, kNewtonSmemMax);
+  set((const void*)k_decide<double, false>, kNewtonSmemMax);
+  set((const void*)k_decide<float, false>, kNewtonSmemMax);
+  set((const void*)k_decide<float, true>, kNewtonSmemMax);
+  set((const void*)k_step<double, false>, kNewtonSmemMax);
+  set((const void*)k_step<float, false>, kNewtonSmemMax);
+  set((const void*)k_step<float, true>, kNewtonSmemMax);
   set((const void*)k_polish<false>, kPolishSmemMax);
   set((const void*)k_polish<true>, kPolishSmemMax);
   {
@@ -1128,7 +1161,6 @@ pc_status pc_destroy(pc_ctx* c) {
   ctx_free(c, c->norms);
   ctx_free(c, c->cnt);
   ctx_free(c, c->g);
-  ctx_free(c, c->cta);
   ctx_free(c, c->dom_buf);
   c->release_extra();
   cudaStreamSynchronize(c->stream);
@@ -1292,9 +1324,10 @@ pc_status pc_stats(pc_ctx* c, int64_t* out, int n_neurons) {
 
 pc_status pc_diagnostics(pc_ctx* c, int64_t* out, int n) {
   if (!c || !out) return PC_ERR_INVALID;
-  const int64_t v[11] = {c->launches, c->grows, c->polished, c->degenerate, c->undecided, c->Vcap,
-                         c->Ecap,    c->Tcap,  (int64_t)c->allocated, c->grid_persist, c->reruns};
-  for (int k = 0; k < n && k < 11; ++k) out[k] = v[k];
+  const int64_t v[13] = {c->launches, c->grows, c->polished, c->degenerate, c->undecided, c->Vcap,
+                         c->Ecap,    c->Tcap,  (int64_t)c->allocated, c->grid_persist, c->reruns, c->flips,
+                         (int64_t)std::ceil(1000.0 * c->flip_margin)};
+  for (int k = 0; k < n && k < 13; ++k) out[k] = v[k];
   return PC_OK;
 }
 
@@ -1341,12 +1374,14 @@ constexpr size_t kNaZBytes = na_align(8ull * kNaMaxWidth * kNaMaxV);
 constexpr size_t kNaOffZ1 = kNaOffZ0 + kNaZBytes;
 constexpr size_t kNaOffEsc = kNaOffZ1 + kNaZBytes;
 constexpr size_t kNaOffExc = kNaOffEsc + na_align(4 * kNaMaxV);
-constexpr size_t kNaOffStage = kNaOffExc + na_align(4 * kNaMaxV);
-constexpr size_t kNaOffTable = kNaOffStage + na_align(16 * kNaMaxE);
-constexpr size_t kNaOffCnt = kNaOffTable + na_align(16 * kNaMaxT);
+constexpr size_t kNaOffList0 = kNaOffExc + na_align(4 * kNaMaxV);
+constexpr size_t kNaOffList1 = kNaOffList0 + na_align(16 * kNaMaxE);
+constexpr size_t kNaFlagBytes = na_align(4 * 2 * (kNaMaxE / 32));
+constexpr size_t kNaOffFlags = kNaOffList1 + na_align(16 * kNaMaxE);
+constexpr size_t kNaOffTable = kNaOffFlags + kNaFlagBytes;
+constexpr size_t kNaOffCnt = kNaOffTable + na_align(32 * kNaMaxT);
 constexpr size_t kNaOffG = kNaOffCnt + na_align(sizeof(Counters) * (kNaMaxN + 1));
-constexpr size_t kNaOffCta = kNaOffG + na_align(sizeof(Global));
-constexpr size_t kNaBytes = kNaOffCta + na_align(8 * 2 * kMaxGrid);
+constexpr size_t kNaBytes = kNaOffG + na_align(sizeof(Global));
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
@@ -1376,6 +1411,11 @@ extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const doub
   if (n > kNaMaxN || p > kNaMaxParams || 2 * D + n > kMaxEntries) return PC_ERR_TOO_LARGE;
   if (cap_v > kNaMaxV || cap_e > kNaMaxE) return PC_ERR_TOO_LARGE;
   if (cap_v < (1 << D) || cap_e < (long long)D << (D - 1)) return PC_ERR_INVALID;
+  // the edge pass reads four endpoints at a time with 16-byte loads from E and
+  // from its second row E + cap_e: both must sit on 16-byte boundaries
+  if (cap_e % 4 != 0 || (reinterpret_cast<uintptr_t>(E) & 15) || (reinterpret_cast<uintptr_t>(X) & 7) ||
+      (reinterpret_cast<uintptr_t>(SIG) & 7))
+    return PC_ERR_INVALID;
   for (int d = 0; d < D; ++d)
     if (!(hi[d] > lo[d])) return PC_ERR_INVALID;
   int dev = 0;
@@ -1449,11 +1489,12 @@ extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const doub
     c.bufs.nz = 2;
     c.bufs.esc = base + kNaOffEsc;
     c.bufs.exc = base + kNaOffExc;
-    c.bufs.stage = base + kNaOffStage;
+    c.bufs.list0 = base + kNaOffList0;
+    c.bufs.list1 = base + kNaOffList1;
+    c.bufs.flags = base + kNaOffFlags;
     c.bufs.table = base + kNaOffTable;
     c.cnt = base + kNaOffCnt;
     c.g = base + kNaOffG;
-    c.cta = base + kNaOffCta;
     c.Vcap = cap_v;
     c.Ecap = cap_e;
     c.Tcap = kNaMaxT;
@@ -1462,7 +1503,8 @@ extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const doub
                                                    reinterpret_cast<float*>(base + kNaOffNorm), p);
     PC_CUDA(cudaGetLastError());
     // the scratch keeps the previous call's contents: reset what must start empty
-    PC_CUDA(cudaMemsetAsync(base + kNaOffTable, 0xff, 16 * kNaMaxT, c.stream));
+    PC_CUDA(cudaMemsetAsync(base + kNaOffTable, 0xff, 32 * kNaMaxT, c.stream));
+    PC_CUDA(cudaMemsetAsync(base + kNaOffFlags, 0, kNaFlagBytes, c.stream));
     PC_CUDA(cudaMemsetAsync(base + kNaOffCnt, 0, sizeof(Counters) * (nn + 1), c.stream));
     c.res_smem = (size_t)newton_ws_doubles(mw, D) * 8;
     occupancy_any(&c);

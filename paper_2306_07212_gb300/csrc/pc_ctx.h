@@ -43,7 +43,9 @@ struct StateBufs {
   void* exc = nullptr;
   void* SIG = nullptr;
   void* E = nullptr;
-  void* stage = nullptr;
+  void* list0 = nullptr;  // splitting edges of the even / odd neurons' steps
+  void* list1 = nullptr;
+  void* flags = nullptr;  // two bitmaps of Ecap bits: edge in list0 / list1
   void* vlist = nullptr;
   void* table = nullptr;
   void* tape_pq = nullptr;
@@ -82,7 +84,6 @@ struct pc_ctx {
   void* cnt = nullptr;
   int cnt_slots = 0;
   void* g = nullptr;
-  void* cta = nullptr;
   void* h_cnt = nullptr;
   void* h_g = nullptr;
 
@@ -103,6 +104,8 @@ struct pc_ctx {
   long long grows = 0;
   long long polished = 0;
   long long launches = 0;
+  long long flips = 0;       // FP64 re-decisions that changed an FP32 sign
+  float flip_margin = 0.f;   // largest |z| / estimate among them
   bool have_result = false;
 
   // per-layer kernel timers (opt.timers)

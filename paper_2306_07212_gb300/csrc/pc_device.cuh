@@ -12,8 +12,11 @@
 //   exc   [Vcap]      float32 estimate of the vertex's coordinate error
 //   SIG   [S][Vcap]   packed sign vectors, 2 bits per entry, word-major
 //   EU/EW [Ecap]      int32 edge endpoints (EW = EU + Ecap)
-//   stage [Ecap]      splitting edges (edge id, V+, V-), staged per CTA range
-//   table [Tcap]      open-addressing hash table of 2-face keys
+//   list  [2][Ecap]   splitting edges (edge id, V+, V-) of a step, two lists
+//                     by neuron parity: one is split while the next neuron's
+//                     is built
+//   flags [2][Ecap/32] bit e set iff edge e is in the list of that parity
+//   table [2][Tcap]   open-addressing hash tables of 2-face keys, by parity
 //   cnt   [N+1]       per-neuron counters (slot n+1 belongs to neuron n)
 #pragma once
 
@@ -81,11 +84,13 @@ struct NetDesc {
   // is hi_d - x_d.
   const double* fA;
   const double* fc;
+  int debug_barrier;     // pc_options.debug_barrier_timeout
 };
 
 struct Counters {        // 128 bytes
   long long nV_before, nE_before;
-  long long nsplit, nkeys, npairs;
+  long long nsplit;      // splitting edges of the step (counted while the previous step runs)
+  long long nkeys, npairs;
   long long nfilter, nundecided, ndegenerate;
   long long tsize;
   long long pruned_e1;   // 0, or 1 + the edge count left by pruning after this step
@@ -96,9 +101,10 @@ struct Global {
   int halted_at;         // -1, or the neuron whose step ran out of capacity
   int halt_reason;
   int error;             // sticky kErr* bits
-  int flip_at;           // last neuron whose FP64 re-decision flipped a sign
+  int flips;             // FP64 re-decisions that changed the FP32 sign
+  int flip_margin_bits;  // largest |z| / (FP32 error estimate) among them (float bits)
   unsigned int barrier;  // grid barrier arrival counter (reset per launch)
-  unsigned int pad1;
+  unsigned int barrier_extra;  // arrivals a barrier waits for beyond the grid: 0, or 1 to test the timeout path
   long long need_v, need_e, need_t;
   long long polished;
   int diag_site;         // first failed consistency check (1 forward product, 2 classify, 3 split), 0: none
@@ -126,13 +132,14 @@ struct State {
   uint64_t* SIG;
   int32_t* EU;
   int32_t* EW;
-  int4* stage;           // splitting edges (edge, V+, V-, 0) staged per CTA range
-  uint64_t* table;       // hash slots: 16 bytes (fingerprint, payload), or 8 bytes (tag | payload) inline
+  int4* list[2];         // splitting edges (edge, V+, V-, 0) of the steps of each neuron parity
+  uint32_t* flags[2];    // bit e of flags[a]: edge e is in list[a]
+  uint64_t* table;       // two hash tables of 2 Tcap words each (neuron parity 0, 1); slots of
+                         // 16 bytes (fingerprint, payload), or 8 bytes (tag | payload) inline
   int4* vlist;           // per edge: (v_a, v_b, zero ordinals, neuron + 1) of a pairing edge, else 0
   int deferred;          // pairings by 64-bit fingerprint, verified after the extraction
   Counters* cnt;
   Global* g;
-  long long* cta_count;
   // interpolation tape (optional): parents and t of every created vertex
   int32_t* tape_pq;      // [2][tape_cap] indexed by vertex id
   double* tape_t;        // [tape_cap]
@@ -207,18 +214,22 @@ __device__ __forceinline__ bool cta_stopped(const State& st) {
 
 // Grid-wide barrier for cooperative launches.  Bounded: after ~0.5 s of
 // waiting it sets kErrTimeout and returns false (the caller then exits).
+// With g->barrier_extra = 1 (a test of this path) the target is one arrival
+// beyond the grid, which never comes, and the limit is 4096 polls.
 __device__ __forceinline__ bool grid_barrier(Global* g, unsigned int& passed) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     passed += 1;
-    const unsigned int target = passed * gridDim.x;
+    const unsigned int extra = *(volatile unsigned int*)&g->barrier_extra;
+    const unsigned int target = passed * gridDim.x + extra;
+    const long long limit = extra ? (1ll << 12) : (1ll << 22);
     __threadfence();
     atomicAdd(&g->barrier, 1u);
     int ok = 1;
     long long spins = 0;
     while (ld_acquire_u32(&g->barrier) < target) {
-      if (++spins > (1ll << 22)) {
+      if (++spins > limit) {
         atomicOr(&g->error, kErrTimeout);
         ok = 0;
         break;

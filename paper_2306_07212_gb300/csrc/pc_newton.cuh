@@ -17,7 +17,10 @@
 namespace pc {
 
 __host__ __device__ constexpr int newton_ws_doubles(int mw, int D) {
-  return 2 * mw + mw * D + D * D + 3 * D + 8 + kMaxWords;  // J, Jn are float
+  // a, an [mw]; J, Jn [mw x D] float; A [D x D], gv, jt [D]; misc; sign words;
+  // then, for the all-rows form, the last layer's values, sums of |terms|
+  // [mw] and gradients [mw x D] float
+  return 2 * mw + mw * D + D * D + 3 * D + 8 + kMaxWords + 2 * mw + (mw * D + 1) / 2;
 }
 
 // Upper bounds of the dynamic shared memory of the kernels that use the
@@ -119,7 +122,11 @@ __device__ inline void newton_solve(const NetDesc& net, const State& st, long lo
 // WARP = false: all threads of the CTA call it; WARP = true: all lanes of one
 // warp call it (ws, s_zl and out private to the warp).  ws holds
 // newton_ws_doubles(mw, D) doubles of shared memory.
-template <bool WARP>
+// ALL: every neuron of layer l_last is evaluated; its value at the stored
+// coordinates, its sum of |terms| and its gradient are left in the all-rows
+// arrays of ws (newton_all_rows), so that the caller can move each value to
+// the exact vertex with the Newton step out->dlt.
+template <bool WARP, bool ALL = false>
 __device__ void newton_group(const NetDesc& net, const State& st, long long v, int e_end, int l_last,
                              int i_target, int mw, double* ws, int* s_zl, NewtonOut* out) {
   const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
@@ -192,7 +199,7 @@ __device__ void newton_group(const NetDesc& net, const State& st, long long v, i
       int zpos = -1;
       for (int q = 0; q < nzc; ++q)
         if (s_zl[q] == entry) zpos = q;
-      const bool need = r < H && (k < l_last || r == i_target || zpos >= 0);
+      const bool need = r < H && (k < l_last || r == i_target || zpos >= 0 || (ALL && k == l_last));
       double acc = 0.0;
       float sc = 0.f, jd[kMaxD];
 #pragma unroll
@@ -226,6 +233,13 @@ __device__ void newton_group(const NetDesc& net, const State& st, long long v, i
           misc[0] = z;
           misc[1] = sc + fabs(b[r]);
           for (int dd = 0; dd < D; ++dd) jt[dd] = jd[dd];
+        }
+        if (ALL && k == l_last) {
+          double* ov = reinterpret_cast<double*>(sig + kMaxWords);
+          ov[r] = z;
+          ov[mw + r] = sc + fabs(b[r]);
+          float* oj = reinterpret_cast<float*>(ov + 2 * mw);
+          for (int dd = 0; dd < D; ++dd) oj[r * D + dd] = jd[dd];
         }
         if (k < l_last) {
           const bool act = ((sig[entry >> 5] >> (2 * (entry & 31))) & 3ull) == kPlus;
@@ -411,6 +425,20 @@ __device__ __forceinline__ void newton_cta(const NetDesc& net, const State& st, 
                                            int l_last, int i_target, int mw, double* ws, int* s_zl,
                                            NewtonOut* out) {
   newton_group<false>(net, st, v, e_end, l_last, i_target, mw, ws, s_zl, out);
+}
+
+// The all-rows arrays of a newton_group<., true> workspace: values at the
+// stored coordinates, sums of |terms| (both mw doubles) and gradients
+// (mw x D floats) of the neurons of layer l_last.
+struct NewtonRows {
+  const double* val;
+  const double* scale;
+  const float* grad;
+};
+__device__ __forceinline__ NewtonRows newton_all_rows(const NetDesc& net, const double* ws, int mw) {
+  const int D = net.D;
+  const double* ov = ws + 2 * mw + mw * D + D * D + 2 * D + 8 + kMaxWords;  // just after the sign words
+  return {ov, ov + mw, reinterpret_cast<const float*>(ov + 2 * mw)};
 }
 
 }  // namespace pc

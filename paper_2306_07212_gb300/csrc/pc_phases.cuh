@@ -1,29 +1,36 @@
 // The per-neuron steps of edge subdivision (Section 4.2) as device functions.
 //
-// One neuron step is two phases separated by grid-wide synchronisation (a
-// kernel boundary in stepwise execution, a grid barrier in the persistent
-// per-layer kernel):
+// A layer l (neurons i = 0 .. H-1, global index n = off_l + i, sign entry
+// e = m + n) runs as
 //
-//   phase_classify  steps (2)+(3).  Every vertex's sign w.r.t. the neuron's
-//       folded hyperplane is written into its sign vector; in the same pass
-//       every edge is classified from the signs of its endpoints' stored
-//       values (splitting iff they differ) and the splitting edges are
-//       compacted per CTA range with warp ballots and a block scan, keeping
-//       edge order.  In mixed precision a |z| within kappa times its FP32
-//       error estimate is re-decided in FP64 at the exact vertex; the edge
-//       pass used the FP32 sign, so if a re-decision flips a sign the step is
-//       marked and the edges are classified again from the final signs
-//       (phase_reclassify) before splitting.
+//   phase_decide   (layer start, once) every value z_j of every current
+//       vertex gets its final sign: an exact zero is a genericity violation
+//       (counted, taken as +); in mixed precision a |z_j| within kappa times
+//       its FP32 error estimate is re-decided in FP64 at the exact vertex.
+//   phase_scan0    (layer start, once) step (3) for neuron 0: the edges whose
+//       endpoints have opposite signs are listed as (edge, V+, V-).
+//   phase_step     (once per neuron, one grid-wide synchronisation each)
+//       steps (4) + (5) for the listed splitting edges of neuron i: new
+//       vertex by interpolation (FP64 t and coordinates), the edge split into
+//       E+ and E-, the parent 2-faces paired in a hash table; and, looking
+//       ahead, step (3) for neuron i + 1: the warp that splits an edge
+//       classifies its two halves and the intersecting edges it creates, the
+//       edge scan classifies every other edge.  So each step starts with its
+//       splitting edges listed and counted, and the capacity check happens
+//       before any write.
+//   phase_pack     (layer end, once) the layer's sign codes of every vertex
+//       are packed into the sign words from the signs of its values.
 //
-//   phase_split  steps (4)+(5).  One warp per splitting edge interpolates the
-//       new vertex (FP64 t and coordinates, values in the value type), splits
-//       the edge into E+ and E-, and inserts the edge's parent 2-face keys
-//       into an open-addressing hash table.  Default: each slot holds the
-//       face's 64-bit fingerprint and the first occurrence's payload, written
-//       with one 128-bit CAS; the second occurrence pairs in the same atomic
-//       and records the pairing, which k_verify_pairs checks exactly after
-//       the last step.  Inline mode: the second occurrence compares the full
-//       face before it pairs.
+// During a layer the sign of a vertex w.r.t. a neuron j of the layer is the
+// sign of its stored value z_j (0 exactly on the folded hyperplane); the
+// values are made consistent with that rule when they are created, so the
+// packed codes equal what step (2) decides.  The sign words hold the earlier
+// layers' entries; a new vertex's words are written complete (earlier layers
+// from its edge's endpoints, this layer from the values) when it is created.
+//
+// A new vertex whose value for a later neuron of the layer is within the FP32
+// filter is re-decided in FP64 by its CTA right after it is created, before
+// anything reads that sign.
 #pragma once
 
 #include "pc_device.cuh"
@@ -31,120 +38,194 @@
 
 namespace pc {
 
-constexpr int kPairCap = 1024;   // intersecting edges a CTA buffers per step
+constexpr int kPairCap = 1024;         // intersecting edges a CTA buffers per step
+constexpr int kPendCap = 2 * kBlock;   // vertices a CTA queues for an FP64 re-decision
 
 struct Smem {
-  long long pref[kMaxGrid + 1];
-  long long wsum[kWarps + 1];
-  long long flist[kFilterCap];
-  int zlist[kWarps][32];
-  int4 pairs[kPairCap];   // (v_partner, v_new, zero ordinals, neuron + 1)
+  long long pend[kPendCap];
+  int4 pairs[kPairCap];                // (v_a, v_b, zero ordinals, neuron + 1)
+  unsigned char pnext[kPairCap];       // bit 0: v_a is - at the next neuron, bit 1: v_b is -
   int npairs;
-  int fcount;
-  int flip;
+  int npend;
+  int zlist[kWarps][16];
   int nzl[kMaxD + 2];
   NewtonOut nout;
   long long acc[4];
 };
 
-__device__ __forceinline__ long long warp_sum_ll(long long x) {
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+template <typename ZT>
+__device__ __forceinline__ ZT tiny_value() {
+  return ZT(1e-30);
+}
+
+// bit 2k of the result = bit k of m
+__device__ __forceinline__ uint64_t spread_even(uint32_t m) {
+  uint64_t x = m;
+  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
   return x;
 }
 
-// Exclusive scan of sm.pref[0..G) in place; sm.pref[G] = total.  G <= kMaxGrid.
-__device__ __forceinline__ void block_scan_pref(Smem& sm, int G) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  constexpr int per = kMaxGrid / kBlock;
-  long long loc[per];
-  long long s = 0;
-#pragma unroll
-  for (int q = 0; q < per; ++q) {
-    const int idx = t * per + q;
-    loc[q] = idx < G ? sm.pref[idx] : 0;
-    s += loc[q];
-  }
-  long long x = s;
-  for (int o = 1; o < 32; o <<= 1) {
-    const long long y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) sm.wsum[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    long long w = lane < kWarps ? sm.wsum[lane] : 0;
-    long long xx = w;
-    for (int o = 1; o < 32; o <<= 1) {
-      const long long y = __shfl_up_sync(0xffffffffu, xx, o);
-      if (lane >= o) xx += y;
-    }
-    if (lane < kWarps) sm.wsum[lane] = xx - w;
-    if (lane == kWarps - 1) sm.wsum[kWarps] = xx;
-  }
-  __syncthreads();
-  long long run = sm.wsum[warp] + (x - s);
-#pragma unroll
-  for (int q = 0; q < per; ++q) {
-    const int idx = t * per + q;
-    if (idx < G) sm.pref[idx] = run;
-    run += loc[q];
-  }
-  if (t == 0) sm.pref[G] = sm.wsum[kWarps];
-  __syncthreads();
+// Bits of word w that hold entries < e_end.
+__device__ __forceinline__ uint64_t entries_below(int w, int e_end) {
+  const int cnt = e_end - 32 * w;
+  if (cnt <= 0) return 0ull;
+  if (cnt >= 32) return ~0ull;
+  return (1ull << (2 * cnt)) - 1ull;
 }
 
-// Block-wide exclusive scan of one small count per thread; returns the
-// thread's offset and leaves the block total in sm.wsum[kWarps].
-__device__ __forceinline__ int block_offsets(Smem& sm, int c) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Vertex and edge counts at the start of step n.
+__device__ __forceinline__ bool step_counts(const State& st, int n, long long& nV, long long& nE) {
+  const Counters* prev = st.cnt + n;
+  nV = prev->nV_before + prev->nsplit;
+  nE = prev->pruned_e1 > 0 ? prev->pruned_e1 - 1 : prev->nE_before + prev->nsplit + prev->npairs;
+  return nV >= 0 && nV <= st.Vcap && nE >= 0 && nE <= st.Ecap;
+}
+
+__device__ __forceinline__ void set_flag(uint32_t* f, long long e) {
+  atomicOr(f + (e >> 5), 1u << (e & 31));
+}
+
+// Appends this lane's `c` (0..2) list entries with one atomic per warp; all
+// lanes must call it.
+__device__ __forceinline__ void warp_append(int c, const int4* ent, int4* list, uint32_t* flags, long long* counter) {
+  const int lane = threadIdx.x & 31;
   int x = c;
   for (int o = 1; o < 32; o <<= 1) {
     const int y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
-  if (lane == 31) sm.wsum[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    const long long w = lane < kWarps ? sm.wsum[lane] : 0;
-    long long xx = w;
-    for (int o = 1; o < 32; o <<= 1) {
-      const long long y = __shfl_up_sync(0xffffffffu, xx, o);
-      if (lane >= o) xx += y;
+  const int tot = __shfl_sync(0xffffffffu, x, 31);
+  if (tot == 0) return;
+  long long base = 0;
+  if (lane == 31) base = atomic_add_ll(counter, (long long)tot);
+  base = __shfl_sync(0xffffffffu, base, 31) + (x - c);
+  for (int t = 0; t < c; ++t) {
+    list[base + t] = ent[t];
+    set_flag(flags, ent[t].x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 re-decision of vertex v's values z_j, j >= j_from, of layer l that lie
+// within the FP32 filter: all threads of the CTA evaluate layer l at the exact
+// vertex (Newton step on its zero set among the entries < e_end) and write
+// back each filtered value with its FP64 sign.
+template <typename ZT>
+__device__ void redecide_cta(const NetDesc& net, const State& st, long long v, int l, int e_end, int j_from,
+                             int mw, double* ws, Smem& sm) {
+  newton_group<false, true>(net, st, v, e_end, l, -1, mw, ws, sm.nzl, &sm.nout);
+  const NewtonRows rows = newton_all_rows(net, ws, mw);
+  const int H = net.w[l + 1], n0 = net.off[l], D = net.D;
+  const long long Vcap = st.Vcap;
+  ZT* Z = static_cast<ZT*>(st.Z[l]);
+  const float esc = st.esc[v];
+  for (int j = j_from + threadIdx.x; j < H; j += blockDim.x) {
+    const float z32 = static_cast<float>(Z[(long long)j * Vcap + v]);
+    const float est = net.nrm[3 * (n0 + j)] * esc + 2.9802322e-8f * net.nrm[3 * (n0 + j) + 1];
+    if (!(fabsf(z32) <= net.kappa * est)) continue;
+    double zs = rows.val[j];
+    if (sm.nout.ok)
+      for (int d = 0; d < D; ++d) zs += static_cast<double>(rows.grad[j * D + d]) * sm.nout.dlt[d];
+    const bool und = !sm.nout.ok || fabs(zs) <= 1e-12 * rows.scale[j];
+    const bool minus = zs < 0.0;
+    ZT zz = static_cast<ZT>(zs);
+    if (!minus && !(zz > ZT(0))) zz = tiny_value<ZT>();
+    if (minus && !(zz < ZT(0))) zz = -tiny_value<ZT>();
+    Z[(long long)j * Vcap + v] = zz;
+    atomic_add_ll(&st.cnt[n0 + j + 1].nfilter, 1ll);
+    if (und) atomic_add_ll(&st.cnt[n0 + j + 1].nundecided, 1ll);
+    if ((z32 < 0.f) != minus) {  // the FP32 sign was wrong: how close to the filter's edge was it?
+      atomicAdd(&st.g->flips, 1);
+      atomicMax(&st.g->flip_margin_bits, __float_as_int(est > 0.f ? fabsf(z32) / est : 0.f));
     }
-    if (lane < kWarps) sm.wsum[lane] = xx - w;
-    if (lane == kWarps - 1) sm.wsum[kWarps] = xx;
   }
   __syncthreads();
-  return int(sm.wsum[warp]) + x - c;
 }
 
-// Tag stored beside each CTA's count: identifies the step that wrote it.
-__device__ __forceinline__ long long cta_tag(int n, long long nE) { return nE * 65536 + n + 1; }
+// Re-decides the CTA's queued vertices one after another and empties the queue.
+template <typename ZT>
+__device__ void drain_pending(const NetDesc& net, const State& st, int l, int e_end, int j_from, int mw, double* ws,
+                              Smem& sm) {
+  const int np = sm.npend;
+  for (int q = 0; q < np; ++q) redecide_cta<ZT>(net, st, sm.pend[q], l, e_end, j_from, mw, ws, sm);
+  __syncthreads();
+  if (threadIdx.x == 0) sm.npend = 0;
+  __syncthreads();
+}
 
-// Edge range of this CTA in the compaction (a multiple of 4 edges per CTA).
-__device__ __forceinline__ void cta_range(long long nE, long long& chunk, long long& begin, long long& end) {
+// ---------------------------------------------------------------------------
+// Layer start, step (2) for every current vertex and every neuron of the
+// layer (values from the layer-start product, step (1)).
+template <typename ZT, bool MIXED>
+__device__ void phase_decide(const NetDesc& net, const State& st, int l, Smem& sm, double* ws, int mw) {
+  const int n0 = net.off[l], H = net.w[l + 1];
+  long long nV, nE;
+  if (!step_counts(st, n0, nV, nE)) {
+    if (threadIdx.x == 0) report_corrupt(st.g, 2, n0, nV, nE, st.Vcap);
+    return;
+  }
+  const long long Vcap = st.Vcap;
+  ZT* Z = static_cast<ZT*>(st.Z[l]);
+  if (threadIdx.x == 0) sm.npend = 0;
+  __syncthreads();
   const long long G = gridDim.x;
-  chunk = ((nE + G - 1) / G + 3) & ~3ll;
-  begin = blockIdx.x * chunk;
-  if (begin > nE) begin = nE;
-  end = begin + chunk < nE ? begin + chunk : nE;
+  for (long long round = 0; round * G * kBlock < nV; ++round) {
+    const long long v = (round * G + blockIdx.x) * kBlock + threadIdx.x;
+    if (v < nV) {
+      bool filt = false;
+      const float esc = MIXED ? st.esc[v] : 0.f;
+      for (int j = 0; j < H; ++j) {
+        ZT z = Z[(long long)j * Vcap + v];
+        if (z == ZT(0)) {  // on a folded hyperplane it was not created on: not generic
+          z = tiny_value<ZT>();
+          Z[(long long)j * Vcap + v] = z;
+          atomic_add_ll(&st.cnt[n0 + j + 1].ndegenerate, 1ll);
+        }
+        if (MIXED)
+          filt = filt || fabsf(static_cast<float>(z)) <=
+                             net.kappa * (net.nrm[3 * (n0 + j)] * esc + 2.9802322e-8f * net.nrm[3 * (n0 + j) + 1]);
+      }
+      if (filt) sm.pend[atomicAdd(&sm.npend, 1)] = v;
+    }
+    if (MIXED) {
+      __syncthreads();
+      if (sm.npend > kPendCap - kBlock) drain_pending<ZT>(net, st, l, net.m + n0, 0, mw, ws, sm);
+    }
+  }
+  if (MIXED) {
+    __syncthreads();
+    drain_pending<ZT>(net, st, l, net.m + n0, 0, mw, ws, sm);
+  }
 }
 
-// Compacts the splitting edges of [begin, end) into stage[begin ...] in edge
-// order as (edge, V+, V-).  FROM_CODES: classify from the stored sign codes
-// (after every sign is final); otherwise from the sign of the stored value.
-template <typename ZT, bool FROM_CODES>
-__device__ long long compact_edges(const State& st, const ZT* zrow, int e, long long begin, long long end,
-                                   long long nV, int n, Smem& sm) {
-  const int sh = 2 * (e & 31);
-  const uint64_t* sw = st.SIG + (long long)(e >> 5) * st.Vcap;
-  long long count = 0;
-  for (long long base = begin; base < end; base += 4 * kBlock) {
-    const long long idx0 = base + 4 * threadIdx.x;
+// ---------------------------------------------------------------------------
+// Step (3) for one neuron over the edges [0, nE): an edge splits iff its
+// endpoints' values in zrow have opposite signs.  Edges flagged in fcur are
+// skipped (they split in the current step, whose warps classify their
+// halves); fcur is cleared on the way.  classify = false only clears.
+template <typename ZT>
+__device__ void scan_edges(const State& st, const ZT* zrow, long long nE, long long nV, uint32_t* fcur,
+                           bool classify, int4* lnext, uint32_t* fnext, long long* counter, int n) {
+  const int lane = threadIdx.x & 31;
+  const long long W = (long long)gridDim.x * kWarps;
+  for (long long tile = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); tile * 128 < nE; tile += W) {
+    const long long idx0 = tile * 128 + 4 * lane;
+    uint32_t skip = 0;
+    if (fcur != nullptr) {
+      const uint32_t fw = idx0 < nE ? fcur[idx0 >> 5] : 0u;
+      skip = (fw >> (idx0 & 31)) & 0xFu;
+      __syncwarp();
+      if ((lane & 7) == 0 && idx0 < nE && fw) fcur[idx0 >> 5] = 0u;
+    }
+    if (!classify) continue;
     int4 eu = make_int4(0, 0, 0, 0), ew = make_int4(0, 0, 0, 0);
     int nvalid = 0;
-    if (idx0 < end) {
-      nvalid = end - idx0 >= 4 ? 4 : int(end - idx0);
+    if (idx0 < nE) {
+      nvalid = nE - idx0 >= 4 ? 4 : int(nE - idx0);
       if (nvalid == 4) {
         eu = *reinterpret_cast<const int4*>(st.EU + idx0);
         ew = *reinterpret_cast<const int4*>(st.EW + idx0);
@@ -159,189 +240,72 @@ __device__ long long compact_edges(const State& st, const ZT* zrow, int e, long 
     }
     const int* pu = &eu.x;
     const int* pw = &ew.x;
-    bool uplus[4], split[4];
+    int4 ent[4];
     int c = 0;
+    uint32_t nib = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      split[q] = false;
-      uplus[q] = true;
-      if (q < nvalid && (pu[q] < 0 || pu[q] >= nV || pw[q] < 0 || pw[q] >= nV)) {
-        report_corrupt(st.g, 6, n, idx0 + q, pu[q], pw[q]);  // never index with it
-      } else if (q < nvalid) {
-        bool su, sv;
-        if (FROM_CODES) {
-          su = ((sw[pu[q]] >> sh) & 3ull) == kMinus;
-          sv = ((sw[pw[q]] >> sh) & 3ull) == kMinus;
-        } else {
-          su = zrow[pu[q]] < ZT(0);
-          sv = zrow[pw[q]] < ZT(0);
-        }
-        split[q] = su != sv;
-        uplus[q] = !su;
-        c += split[q];
+      if (q >= nvalid || ((skip >> q) & 1u)) continue;
+      const int u = pu[q], w = pw[q];
+      if (u < 0 || u >= nV || w < 0 || w >= nV) {
+        report_corrupt(st.g, 6, n, idx0 + q, u, w);  // never index with it
+        continue;
+      }
+      const bool su = zrow[u] < ZT(0), sv = zrow[w] < ZT(0);
+      if (su != sv) {
+        ent[c++] = make_int4(int(idx0 + q), su ? w : u, su ? u : w, 0);
+        nib |= 1u << q;
       }
     }
-    const int off = block_offsets(sm, c);
-    int k = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (split[q]) {
-        const int p = uplus[q] ? pu[q] : pw[q];
-        const int mq = uplus[q] ? pw[q] : pu[q];
-        st.stage[begin + count + off + k] = make_int4(int(idx0 + q), p, mq, 0);
-        ++k;
-      }
+    int x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    count += sm.wsum[kWarps];
-    __syncthreads();
+    const int tot = __shfl_sync(0xffffffffu, x, 31);
+    if (tot == 0) continue;
+    long long base = 0;
+    if (lane == 31) base = atomic_add_ll(counter, (long long)tot);
+    base = __shfl_sync(0xffffffffu, base, 31) + (x - c);
+    for (int t = 0; t < c; ++t) lnext[base + t] = ent[t];
+    uint32_t word = nib << (idx0 & 31);  // the 8 lanes of a flag word OR their nibbles
+    word |= __shfl_xor_sync(0xffffffffu, word, 1);
+    word |= __shfl_xor_sync(0xffffffffu, word, 2);
+    word |= __shfl_xor_sync(0xffffffffu, word, 4);
+    if ((lane & 7) == 0 && word) atomicOr(fnext + (idx0 >> 5), word);
   }
-  return count;
+}
+
+// Layer start, step (3) for neuron 0 of layer l.
+template <typename ZT>
+__device__ void phase_scan0(const NetDesc& net, const State& st, int l) {
+  const int n0 = net.off[l];
+  long long nV, nE;
+  if (!step_counts(st, n0, nV, nE)) {
+    if (threadIdx.x == 0) report_corrupt(st.g, 2, n0, nV, nE, st.Vcap);
+    return;
+  }
+  const ZT* zrow = static_cast<const ZT*>(st.Z[l]);
+  scan_edges<ZT>(st, zrow, nE, nV, nullptr, true, st.list[n0 & 1], st.flags[n0 & 1], &st.cnt[n0 + 1].nsplit, n0);
 }
 
 // ---------------------------------------------------------------------------
-// Steps (2)+(3).
-template <typename ZT, bool MIXED>
-__device__ void phase_classify(const NetDesc& net, const State& st, int zb, int l, int i, int n,
-                               Smem& sm, double* ws, int mw) {
-  const Counters* prev = st.cnt + n;
-  const long long nV = prev->nV_before + prev->nsplit;
-  const long long nE = prev->pruned_e1 > 0 ? prev->pruned_e1 - 1 : prev->nE_before + prev->nsplit + prev->npairs;
-  Counters* cur = st.cnt + n + 1;
-  if (nV < 0 || nV > st.Vcap || nE < 0 || nE > st.Ecap) {
-    if (threadIdx.x == 0) report_corrupt(st.g, 2, n, nV, nE, st.Vcap);
-    return;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    cur->nV_before = nV;
-    cur->nE_before = nE;
-  }
-  const long long Vcap = st.Vcap;
-  ZT* Z = static_cast<ZT*>(st.Z[zb]);
-  const ZT* zrow = Z + (long long)i * Vcap;
-  const int e = net.m + n, sh = 2 * (e & 31);
-  uint64_t* sw = st.SIG + (long long)(e >> 5) * Vcap;
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    sm.fcount = 0;
-    sm.flip = 0;
-  }
-  __syncthreads();
-  long long ndeg = 0;
-  int und = 0;
-  // FP64 re-decision of the CTA's filtered vertices, one at a time with all
-  // threads cooperating (newton_cta).
-  auto drain = [&]() {
-    const int fc = sm.fcount;
-    for (int q = 0; q < fc; ++q) {
-      const long long v = sm.flist[q];
-      newton_cta(net, st, v, e, l, i, mw, ws, sm.nzl, &sm.nout);
-      if (threadIdx.x == 0) {
-        const double zs = sm.nout.z;
-        if (fabs(zs) <= 1e-12 * sm.nout.scale || !sm.nout.ok) ++und;
-        const uint64_t code = zs < 0.0 ? kMinus : kPlus;
-        const bool spec_minus = zrow[v] < ZT(0);
-        if (spec_minus != (code == kMinus)) sm.flip = 1;
-        sw[v] = (sw[v] & ~(3ull << sh)) | (code << sh);
-        ZT zz = static_cast<ZT>(zs);
-        if (code == kPlus && !(zz > ZT(0))) zz = ZT(1e-30);
-        if (code == kMinus && !(zz < ZT(0))) zz = ZT(-1e-30);
-        Z[(long long)i * Vcap + v] = zz;
-      }
-    }
-    if (threadIdx.x == 0 && fc > 0) atomic_add_ll(&cur->nfilter, (long long)fc);
-    __syncthreads();
-    if (threadIdx.x == 0) sm.fcount = 0;
-    __syncthreads();
-  };
-  const float nr_i = net.nrm[3 * n], b_i = 2.9802322e-8f * net.nrm[3 * n + 1];
-  // step (2): the signs; 32-vertex tiles are dealt round-robin over the CTAs
-  // so that neighbouring vertices (often filtered together) spread out
-  const long long G = gridDim.x;
-  const int warp = threadIdx.x >> 5;
-  for (long long round = 0; round * G * kBlock < nV; ++round) {
-    const long long v = ((round * kWarps + warp) * G + blockIdx.x) * 32 + lane;
-    if (v < nV) {
-      const ZT z = zrow[v];
-      bool filt = false;
-      if (MIXED) filt = fabsf(static_cast<float>(z)) <= net.kappa * (nr_i * st.esc[v] + b_i);
-      if (filt) {
-        const int slot = atomicAdd(&sm.fcount, 1);
-        sm.flist[slot] = v;
-      } else {
-        const uint64_t code = (z < ZT(0)) ? kMinus : kPlus;
-        ndeg += (z == ZT(0));
-        sw[v] = (sw[v] & ~(3ull << sh)) | (code << sh);
-      }
-    }
-    if (MIXED) {
-      __syncthreads();
-      if (sm.fcount > kFilterCap - kBlock) drain();
-    }
-  }
-  if (MIXED) {
-    __syncthreads();
-    drain();
-    if (threadIdx.x == 0 && sm.flip) atomicMax(&st.g->flip_at, n);
-  }
-  // the part of the hash table that the previous neuron used
-  const long long tprev = 2 * st.cnt[n].tsize;  // 16-byte slots (the inline mode uses the first half)
-  for (long long t = (long long)blockIdx.x * kBlock + threadIdx.x; t < tprev; t += (long long)gridDim.x * kBlock)
-    st.table[t] = kEmpty;
-  // step (3): splitting edges, speculatively from the signs of the values
-  long long chunk, begin, end;
-  cta_range(nE, chunk, begin, end);
-  const long long count = compact_edges<ZT, false>(st, zrow, e, begin, end, nV, n, sm);
-  if (threadIdx.x == 0) {
-    st.cta_count[blockIdx.x] = count;
-    st.cta_count[kMaxGrid + blockIdx.x] = cta_tag(n, nE);
-  }
-  ndeg = warp_sum_ll(ndeg);
-  if (lane == 0 && ndeg) atomic_add_ll(&cur->ndegenerate, ndeg);
-  if (MIXED && threadIdx.x == 0 && und) atomic_add_ll(&cur->nundecided, (long long)und);
-}
-
-// Step (3) again from the final sign codes, for a step whose FP64 re-decision
-// flipped a sign that the speculative pass had used.
-__device__ __forceinline__ void phase_reclassify(const NetDesc& net, const State& st, int n, Smem& sm) {
-  const long long nV = st.cnt[n + 1].nV_before, nE = st.cnt[n + 1].nE_before;
-  long long chunk, begin, end;
-  cta_range(nE, chunk, begin, end);
-  const long long count = compact_edges<float, true>(st, nullptr, net.m + n, begin, end, nV, n, sm);
-  if (threadIdx.x == 0) {
-    st.cta_count[blockIdx.x] = count;
-    st.cta_count[kMaxGrid + blockIdx.x] = cta_tag(n, nE);
-  }
-}
-
-// Whole-warp check that the 2-face key of split edge k2 (payload r2 =
-// 2 * zero ordinal + minus) equals F, where lane w holds word w of the
+// Whole-warp check (inline pairing) that the 2-face key of split k2 (payload
+// r2 = 2 * zero ordinal + minus) equals F, where lane w holds word w of this
 // splitting edge's sign vector s0 and F is s0 with word wj replaced by Fw.
-// The partner's key is rebuilt from its staged endpoints, which this phase
-// does not modify, so no memory fence is needed.  All lanes must call it.
-__device__ __forceinline__ bool warp_face_matches(const State& st, const Smem& sm, int G, long long chunk,
-                                                  long long k2, int r2, int e, int S, uint64_t s0,
+// The partner's face is rebuilt from its new vertex's sign words, which the
+// partner wrote (and fenced) before it inserted its key.  All lanes call it.
+__device__ __forceinline__ bool warp_face_matches(const State& st, long long k2, int r2, int e, int S, uint64_t s0,
                                                   int wj, uint64_t Fw, long long nV, long long total, int n) {
   const int lane = threadIdx.x & 31;
   if (k2 < 0 || k2 >= total) {  // a payload that no split of this step wrote
     if (lane == 0) report_corrupt(st.g, 5, n, k2, total, r2);
     return false;
   }
-  int lo = 0, hi = G - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (sm.pref[mid] <= k2) lo = mid; else hi = mid - 1;
-  }
-  const int4 s2 = st.stage[lo * chunk + (k2 - sm.pref[lo])];
-  if (s2.y < 0 || s2.y >= nV || s2.z < 0 || s2.z >= nV) {
-    if (lane == 0) report_corrupt(st.g, 7, n, k2, s2.y, s2.z);
-    return false;
-  }
-  const long long Vcap = st.Vcap;
-  const int wn = e >> 5, sh = 2 * (e & 31);
+  const long long v2 = nV + k2;
   uint64_t w2 = 0, zm = 0;
   if (lane < S) {
-    w2 = st.SIG[(long long)lane * Vcap + s2.y] | st.SIG[(long long)lane * Vcap + s2.z];
-    if (lane == wn) w2 &= ~(3ull << sh);
+    w2 = __ldcg(st.SIG + (long long)lane * st.Vcap + v2);
     zm = zero_mask(w2, lane, e);
   }
   const int c = __popcll(zm);
@@ -369,36 +333,23 @@ __device__ __forceinline__ bool warp_face_matches(const State& st, const Smem& s
 }
 
 // ---------------------------------------------------------------------------
-// Steps (4)+(5).  Returns true when capacity ran out (nothing written).
+// One neuron step: steps (4)+(5) for the listed splitting edges, step (3) for
+// the next neuron.  Returns true when the step must not run (capacity ran out
+// -- nothing has been written -- or a counter is corrupt); the caller exits.
 template <typename ZT, bool MIXED>
-__device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, int i, int n, Smem& sm) {
+__device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Smem& sm, double* ws, int mw) {
   constexpr bool TRACK = sizeof(ZT) == 4;  // FP32 values carry error estimates
+  const int n = net.off[l] + i;
+  const int H = net.w[l + 1];
+  const bool ahead = i + 1 < H;
   Counters* cur = st.cnt + n + 1;
-  const long long nV = cur->nV_before, nE = cur->nE_before;
-  const int G = gridDim.x;
-  {
-    // every CTA range of this step must carry a count written for this step
-    long long chunk0, b0_, b1_;
-    cta_range(nE, chunk0, b0_, b1_);
-    int bad = 0;
-    for (int q = threadIdx.x; q < G; q += kBlock) {
-      const long long cq = st.cta_count[q], tq = st.cta_count[kMaxGrid + q];
-      sm.pref[q] = cq;
-      if (tq != cta_tag(n, nE) || cq < 0 || cq > chunk0) {
-        report_corrupt(st.g, 8, n, q, tq, cq);
-        bad = 1;
-      }
-    }
-    if (__syncthreads_or(bad)) return true;
+  long long nV, nE;
+  if (!step_counts(st, n, nV, nE)) {
+    if (threadIdx.x == 0) report_corrupt(st.g, 2, n, nV, nE, st.Vcap);
+    return true;
   }
-  if (threadIdx.x == 0) {
-    sm.npairs = 0;
-    sm.acc[0] = sm.acc[1] = 0;
-  }
-  __syncthreads();
-  block_scan_pref(sm, G);
-  const long long total = sm.pref[G];
-  if (total < 0 || total > nE || nV < 0 || nV > st.Vcap || nE > st.Ecap) {
+  const long long total = cur->nsplit;
+  if (total < 0 || total > nE) {
     if (threadIdx.x == 0) report_corrupt(st.g, 3, n, total, nV, nE);
     return true;
   }
@@ -426,151 +377,206 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
     return true;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    cur->nsplit = total;
+    cur->nV_before = nV;
+    cur->nE_before = nE;
     cur->tsize = tneed;
   }
+  if (threadIdx.x == 0) {
+    sm.npairs = 0;
+    sm.npend = 0;
+    sm.acc[0] = sm.acc[1] = 0;
+  }
+  // the table of the previous step: emptied for the step after this one
+  {
+    uint64_t* told = st.table + (long long)((n + 1) & 1) * 2 * st.Tcap;
+    const long long tprev = 2 * st.cnt[n].tsize;
+    for (long long t = (long long)blockIdx.x * kBlock + threadIdx.x; t < tprev; t += (long long)gridDim.x * kBlock)
+      told[t] = kEmpty;
+  }
+  __syncthreads();
   const long long Vcap = st.Vcap;
-  long long chunk, b0, b1;
-  cta_range(nE, chunk, b0, b1);
-  const int H = net.w[l + 1];
-  ZT* Z = static_cast<ZT*>(st.Z[zb]);
+  ZT* Z = static_cast<ZT*>(st.Z[l]);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int e = m + n, wn = e >> 5, sh = 2 * (e & 31);
-  int* zlist = sm.zlist[warp];
+  const int e = m + n;
+  const int e0 = m + net.off[l];
+  const int4* lcur = st.list[n & 1];
+  int4* lnext = st.list[(n + 1) & 1];
+  uint32_t* fnext = st.flags[(n + 1) & 1];
+  long long* cnext = ahead ? &st.cnt[n + 2].nsplit : nullptr;
+  uint64_t* table = st.table + (long long)(n & 1) * 2 * st.Tcap;
   const long long tmask = tneed - 1;
+  const float* nrl = net.nrm + 3 * net.off[l];
+  int* zlist = sm.zlist[warp];
   long long nkeys_w = 0, ndeg_w = 0;
   int err_w = 0;
-  for (long long k = (long long)blockIdx.x * kWarps + warp; k < total; k += (long long)G * kWarps) {
-    int lo = 0, hi = G - 1;
-    while (lo < hi) {  // largest q with pref[q] <= k
-      const int mid = (lo + hi + 1) >> 1;
-      if (sm.pref[mid] <= k) lo = mid; else hi = mid - 1;
-    }
-    const int4 sg = st.stage[lo * chunk + (k - sm.pref[lo])];
-    const int32_t ed = sg.x, p = sg.y, q = sg.z;  // p: V+, q: V-
-    if (ed < 0 || ed >= nE || p < 0 || p >= nV || q < 0 || q >= nV) {  // warp-uniform
-      if (lane == 0) report_corrupt(st.g, 4, n, ed, p, q);
-      continue;
-    }
-    // every endpoint load is issued before any of them is used
-    const ZT za0 = Z[(long long)i * Vcap + p], zb0 = Z[(long long)i * Vcap + q];
-    double xp = 0.0, xq = 0.0;
-    if (lane < D) {
-      xp = st.X[(long long)lane * Vcap + p];
-      xq = st.X[(long long)lane * Vcap + q];
-    }
-    uint64_t sp = 0, sq = 0;
-    if (lane < S) {
-      sp = st.SIG[(long long)lane * Vcap + p];
-      sq = st.SIG[(long long)lane * Vcap + q];
-    }
-    ZT zpa = ZT(0), zqa = ZT(0), zpb = ZT(0), zqb = ZT(0);  // rows lane and lane + 32 of the first 64
-    if (lane < H) {
-      zpa = Z[(long long)lane * Vcap + p];
-      zqa = Z[(long long)lane * Vcap + q];
-    }
-    if (lane + 32 < H) {
-      zpb = Z[(long long)(lane + 32) * Vcap + p];
-      zqb = Z[(long long)(lane + 32) * Vcap + q];
-    }
-    float rp = 0.f, rq = 0.f, xep = 0.f, xeq = 0.f;
-    if (TRACK && lane == 0) {
-      rp = st.esc[p];
-      rq = st.esc[q];
-      xep = st.exc[p];
-      xeq = st.exc[q];
-    }
-    const double a = static_cast<double>(za0);
-    const double b = static_cast<double>(zb0);
-    double t = a / (a - b);
-    bool bad = !(a > 0.0 && b < 0.0);
-    if (!(t >= 0.0 && t <= 1.0)) { t = t < 0.0 ? 0.0 : 1.0; bad = true; }
+  const long long G = gridDim.x;
+  const long long Wt = G * kWarps;
+  const long long rounds = (total + Wt - 1) / Wt;
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long k = rd * Wt + (long long)warp * G + blockIdx.x;  // splits dealt over the CTAs first
+    // ---- part A: the new vertex (step (4)) ----
+    bool okA = false, pend = false, bad = false;
+    int32_t ed = 0, p = 0, q = 0;
     const int32_t v0 = int32_t(nV + k);
-    if (lane < D) st.X[(long long)lane * Vcap + v0] = fma(t, xq - xp, xp);
-    const ZT tz = static_cast<ZT>(t);
-    const float* nrl = net.nrm + 3 * net.off[l];
-    float amax = 0.f;
-    for (int j0 = 0; j0 < H; j0 += 64) {
-      const int ja = j0 + lane, jb = ja + 32;
-      if (j0 > 0) {
-        zpa = zqa = zpb = zqb = ZT(0);
-        if (ja < H) {
-          zpa = Z[(long long)ja * Vcap + p];
-          zqa = Z[(long long)ja * Vcap + q];
-        }
-        if (jb < H) {
-          zpb = Z[(long long)jb * Vcap + p];
-          zqb = Z[(long long)jb * Vcap + q];
-        }
-      }
-      const ZT za = (ja == i) ? ZT(0) : zpa + tz * (zqa - zpa);
-      const ZT zb2 = (jb == i) ? ZT(0) : zpb + tz * (zqb - zpb);
-      if (ja < H) Z[(long long)ja * Vcap + v0] = za;
-      if (jb < H) Z[(long long)jb * Vcap + v0] = zb2;
-      if (TRACK) {  // the rounding of z_j, in units of ||W_j||_2
-        if (ja < H) amax = fmaxf(amax, fabsf(static_cast<float>(za)) * nrl[3 * ja + 2]);
-        if (jb < H) amax = fmaxf(amax, fabsf(static_cast<float>(zb2)) * nrl[3 * jb + 2]);
-      }
-    }
-    if (TRACK) {
-      // error estimates: values (rounding of the interpolation) and position
-      // (a t computed from values carrying the endpoints' estimates)
-      for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-      float dx = lane < D ? static_cast<float>(fabs(xq - xp)) : 0.f;
-      for (int o = 16; o > 0; o >>= 1) dx = fmaxf(dx, __shfl_xor_sync(0xffffffffu, dx, o));
-      if (lane == 0) {
-        // rms estimates, independent errors adding in quadrature.  value
-        // scale: the endpoints' scales (the convex combination does not
-        // amplify them) and the interpolation's rounding (u of |z_j|, in units
-        // of ||W_j||_2).
-        // position: the shift along the edge that the errors of a and b cause
-        // in t = a / (a - b), added in quadrature to the endpoints' position
-        // estimates (independent errors; the convex combination does not
-        // amplify the endpoints' own errors).
-        const float rm = fmaxf(rp, rq), rr = 5.9604645e-8f * amax;
-        st.esc[v0] = sqrtf(rm * rm + rr * rr);
-        const float ep = nrl[3 * i] * rp + 2.9802322e-8f * nrl[3 * i + 1];
-        const float eq = nrl[3 * i] * rq + 2.9802322e-8f * nrl[3 * i + 1];
-        const float shift = static_cast<float>((ep + eq) / (a - b)) * dx;
-        const float xe = fmaxf(xep, xeq);
-        st.exc[v0] = sqrtf(xe * xe + shift * shift);
-      }
-    }
-    // sign vector of the new vertex: join of the endpoints, entry n := 0
     uint64_t s0 = 0, zm = 0;
-    if (lane < S) {
+    ZT zpn = ZT(0), zqn = ZT(0), z0n = ZT(0);  // values at neuron i + 1
+    if (k < total) {
+      const int4 sg = lcur[k];
+      ed = sg.x;
+      p = sg.y;  // V+
+      q = sg.z;  // V-
+      okA = !(ed < 0 || ed >= nE || p < 0 || p >= nV || q < 0 || q >= nV);  // warp-uniform
+      if (!okA && lane == 0) report_corrupt(st.g, 4, n, ed, p, q);
+    }
+    if (okA) {
+      const ZT za0 = Z[(long long)i * Vcap + p], zb0 = Z[(long long)i * Vcap + q];
+      double xp = 0.0, xq = 0.0;
+      if (lane < D) {
+        xp = st.X[(long long)lane * Vcap + p];
+        xq = st.X[(long long)lane * Vcap + q];
+      }
+      uint64_t sp = 0, sq = 0;
+      if (lane < S) {
+        sp = st.SIG[(long long)lane * Vcap + p];
+        sq = st.SIG[(long long)lane * Vcap + q];
+      }
+      float rp = 0.f, rq = 0.f, xep = 0.f, xeq = 0.f;
+      if (TRACK && lane == 0) {
+        rp = st.esc[p];
+        rq = st.esc[q];
+        xep = st.exc[p];
+        xeq = st.exc[q];
+      }
+      const double a = static_cast<double>(za0);
+      const double b = static_cast<double>(zb0);
+      double t = a / (a - b);
+      bad = !(a > 0.0 && b < 0.0);
+      if (!(t >= 0.0 && t <= 1.0)) {
+        t = t < 0.0 ? 0.0 : 1.0;
+        bad = true;
+      }
+      if (lane < D) st.X[(long long)lane * Vcap + v0] = fma(t, xq - xp, xp);
+      const ZT tz = static_cast<ZT>(t);
+      // earlier layers' entries: the join of the endpoints' words
+      const uint64_t below = lane < S ? entries_below(lane, e0) : 0ull;
       uint64_t conf = ((sp & kEvenBits) & ((sq >> 1) & kEvenBits)) | ((sq & kEvenBits) & ((sp >> 1) & kEvenBits));
-      s0 = sp | sq;
-      if (lane == wn) {
-        conf &= ~(1ull << sh);
-        s0 &= ~(3ull << sh);
+      if (conf & below) err_w |= kErrConflict;
+      s0 = (sp | sq) & below;
+      float amax = 0.f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (64 * c >= H) continue;  // warp-uniform
+        uint32_t plus2[2], minus2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = 64 * c + 32 * h + lane;
+          ZT zp = ZT(0), zq = ZT(0), zj = ZT(0);
+          bool pl = false, mi = false;
+          if (j < H) {
+            zp = Z[(long long)j * Vcap + p];
+            zq = Z[(long long)j * Vcap + q];
+            if (j < i) {  // processed: the join of the endpoints' signs, value made consistent
+              pl = zp > ZT(0) || zq > ZT(0);
+              mi = zp < ZT(0) || zq < ZT(0);
+              if (pl && mi) err_w |= kErrConflict;
+              zj = zp + tz * (zq - zp);
+              if (pl && !(zj > ZT(0))) zj = tiny_value<ZT>();
+              if (mi && !(zj < ZT(0))) zj = -tiny_value<ZT>();
+              if (!pl && !mi) zj = ZT(0);
+            } else if (j > i) {
+              zj = zp + tz * (zq - zp);
+              if (zj == ZT(0)) {  // on a later folded hyperplane: not generic
+                zj = tiny_value<ZT>();
+                atomic_add_ll(&st.cnt[net.off[l] + j + 1].ndegenerate, 1ll);
+              }
+            }
+            Z[(long long)j * Vcap + v0] = zj;  // row i: exactly 0
+            if (TRACK) amax = fmaxf(amax, fabsf(static_cast<float>(zj)) * nrl[3 * j + 2]);
+          }
+          plus2[h] = __ballot_sync(0xffffffffu, pl);
+          minus2[h] = __ballot_sync(0xffffffffu, mi);
+          if (ahead && 64 * c + 32 * h <= i + 1 && i + 1 < 64 * c + 32 * h + 32) {  // warp-uniform
+            const int src = (i + 1) & 31;
+            zpn = __shfl_sync(0xffffffffu, zp, src);
+            zqn = __shfl_sync(0xffffffffu, zq, src);
+            z0n = __shfl_sync(0xffffffffu, zj, src);
+          }
+        }
+        // this chunk's codes (entries e0 + 64c ...) into the lane's word
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint64_t il = spread_even(plus2[h]) | (spread_even(minus2[h]) << 1);
+          if (!il) continue;
+          const int ent = e0 + 64 * c + 32 * h, w = ent >> 5, s = 2 * (ent & 31);
+          if (lane == w) s0 |= il << s;
+          if (s && lane == w + 1) s0 |= il >> (64 - s);
+        }
       }
-      if (conf) err_w |= kErrConflict;
-      st.SIG[(long long)lane * Vcap + v0] = s0;
-      zm = zero_mask(s0, lane, e);
-    }
-    if (lane == 0) {
-      st.EU[ed] = p;
-      st.EW[ed] = v0;
-      st.EU[nE + k] = q;
-      st.EW[nE + k] = v0;
-      if (st.deferred) st.vlist[nE + k] = make_int4(0, 0, 0, 0);  // not a pairing edge
-      if (st.keep_tape) {
-        st.tape_pq[v0] = p;
-        st.tape_pq[st.tape_cap + v0] = q;
-        st.tape_t[v0] = t;
+      if (TRACK) {
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        float dx = lane < D ? static_cast<float>(fabs(xq - xp)) : 0.f;
+        for (int o = 16; o > 0; o >>= 1) dx = fmaxf(dx, __shfl_xor_sync(0xffffffffu, dx, o));
+        float esc0 = 0.f;
+        if (lane == 0) {
+          // rms estimates, independent errors adding in quadrature: the value
+          // scale takes the endpoints' (a convex combination does not amplify
+          // them) and the interpolation's rounding (u |z_j|, in units of
+          // ||W_j||_2); the position takes the endpoints' estimates and the
+          // shift along the edge that the errors of a and b cause in t.
+          const float rm = fmaxf(rp, rq), rr = 5.9604645e-8f * amax;
+          esc0 = sqrtf(rm * rm + rr * rr);
+          st.esc[v0] = esc0;
+          const float ep = nrl[3 * i] * rp + 2.9802322e-8f * nrl[3 * i + 1];
+          const float eq = nrl[3 * i] * rq + 2.9802322e-8f * nrl[3 * i + 1];
+          const float shift = static_cast<float>((ep + eq) / (a - b)) * dx;
+          const float xe = fmaxf(xep, xeq);
+          st.exc[v0] = sqrtf(xe * xe + shift * shift);
+        }
+        if (MIXED) {  // this lane's new values of the later neurons, as it wrote them
+          esc0 = __shfl_sync(0xffffffffu, esc0, 0);
+          bool f = false;
+          for (int j = lane; j < H; j += 32)
+            if (j > i)
+              f = f || fabsf(static_cast<float>(Z[(long long)j * Vcap + v0])) <=
+                           net.kappa * (nrl[3 * j] * esc0 + 2.9802322e-8f * nrl[3 * j + 1]);
+          pend = __any_sync(0xffffffffu, f);
+        }
+      }
+      if (lane < S) {
+        st.SIG[(long long)lane * Vcap + v0] = s0;
+        zm = zero_mask(s0, lane, e);
+      }
+      if (lane == 0) {
+        st.EU[ed] = p;
+        st.EW[ed] = v0;
+        st.EU[nE + k] = q;
+        st.EW[nE + k] = v0;
+        if (st.deferred) st.vlist[nE + k] = make_int4(0, 0, 0, 0);  // not a pairing edge
+        if (st.keep_tape) {
+          st.tape_pq[v0] = p;
+          st.tape_pq[st.tape_cap + v0] = q;
+          st.tape_t[v0] = t;
+        }
+        if (pend) sm.pend[atomicAdd(&sm.npend, 1)] = v0;
       }
     }
-    // zero entries of the splitting edge (D-1 of them under genericity)
-    const int c = __popcll(zm);
-    int x = c;
+    if (MIXED) {  // FP64 re-decisions of this round's new vertices (uniform per CTA)
+      __syncthreads();
+      if (sm.npend > 0) drain_pending<ZT>(net, st, l, e + 1, i + 1, mw, ws, sm);
+    }
+    if (!okA) continue;
+    // ---- part B: the parent 2-faces (step (5)) and the look-ahead ----
+    if (ahead && pend) z0n = Z[(long long)(i + 1) * Vcap + v0];  // re-decided by this CTA
+    const bool m0n = z0n < ZT(0);
+    const int c0 = __popcll(zm);
+    int x = c0;
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
     const int nz = __shfl_sync(0xffffffffu, x, 31);
     {
-      int kk = x - c;
+      int kk = x - c0;
       uint64_t mm = zm;
       while (mm) {
         const int bit = __ffsll((long long)mm) - 1;
@@ -591,7 +597,7 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
     const uint64_t s0w = __shfl_sync(0xffffffffu, s0, wj);
     const bool has_key = (nz == D - 1) && (o < nz) && !(minus && jz < m);
     nkeys_w += __popc(__ballot_sync(0xffffffffu, has_key));
-    if (bad) ndeg_w += 1;
+    if (bad) ndeg_w += (lane == 0);
     uint64_t Fw = 0, h = 0;
     long long slot = 0;
     if (has_key) {
@@ -602,13 +608,13 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
     if (st.deferred) {
       // Full 64-bit fingerprint and payload in one 16-byte slot: the first
       // arrival inserts both with one 128-bit CAS, the second finds the
-      // partner in the same atomic and pairs at once.  Every pairing is
-      // re-checked exactly after the extraction (k_verify_pairs) from the
-      // two new vertices' sign vectors.
+      // partner (and its sign at the next neuron, bit 62) in the same atomic
+      // and pairs at once.  Every pairing is re-checked exactly after the
+      // extraction (k_verify_pairs) from the two new vertices' sign vectors.
       if (has_key) {
         if (h == kEmpty) h = kEmpty - 1;
-        const unsigned long long mine = uint64_t(k) * R + uint64_t(lane);
-        unsigned long long* tb = reinterpret_cast<unsigned long long*>(st.table);
+        const unsigned long long mine = (uint64_t(k) * R + uint64_t(lane)) | (m0n ? (1ull << 62) : 0ull);
+        unsigned long long* tb = reinterpret_cast<unsigned long long*>(table);
         for (long long probes = 0;; ++probes) {
           if (probes > tneed) {
             err_w |= kErrProbe;
@@ -622,17 +628,25 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
             if (prev & kPaired64) {
               err_w |= kErrPairing;
             } else {
-              const long long k2 = (long long)((ov & ~kPaired64) / R);
-              const int r2 = int((ov & ~kPaired64) % R);
+              const unsigned long long pay = ov & ~(kPaired64 | (1ull << 62));
+              const long long k2 = (long long)(pay / R);
+              const int r2 = int(pay % R);
               const int4 rec = make_int4(int(nV + k2), v0, (r2 << 16) | lane, n + 1);
+              const unsigned char nx = ((ov >> 62) & 1ull ? 1 : 0) | (m0n ? 2 : 0);
               const int slot2 = atomicAdd(&sm.npairs, 1);
               if (slot2 < kPairCap) {
                 sm.pairs[slot2] = rec;
+                sm.pnext[slot2] = nx;
               } else {
-                const long long idx = atomic_add_ll(&cur->npairs, 1ll);
-                st.EU[nE + total + idx] = rec.x;
-                st.EW[nE + total + idx] = rec.y;
-                st.vlist[nE + total + idx] = rec;
+                const long long idx = nE + total + atomic_add_ll(&cur->npairs, 1ll);
+                st.EU[idx] = rec.x;
+                st.EW[idx] = rec.y;
+                st.vlist[idx] = rec;
+                if (ahead && ((nx ^ (nx >> 1)) & 1)) {
+                  const long long b2 = atomic_add_ll(cnext, 1ll);
+                  lnext[b2] = (nx & 1) ? make_int4(int(idx), rec.y, rec.x, 0) : make_int4(int(idx), rec.x, rec.y, 0);
+                  set_flag(fnext, idx);
+                }
               }
             }
             break;
@@ -641,6 +655,11 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
         }
       }
     } else {
+      // Inline: a 32-bit tag; the second arrival compares the full faces
+      // before it pairs.  The partner's sign words and value at the next
+      // neuron are read from memory, so they are fenced before the insert.
+      __threadfence();
+      __syncwarp();
       const uint32_t tag = uint32_t(h >> 32);
       const uint64_t mine = has_key ? ((uint64_t(tag) << 32) | (uint64_t(k) * R + uint64_t(lane))) : 0ull;
       bool active = has_key;
@@ -649,7 +668,7 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
         bool cand = false;
         uint64_t old = 0;
         if (active) {
-          old = atomicCAS(reinterpret_cast<unsigned long long*>(st.table + slot), (unsigned long long)kEmpty,
+          old = atomicCAS(reinterpret_cast<unsigned long long*>(table + slot), (unsigned long long)kEmpty,
                           (unsigned long long)mine);
           if (old == kEmpty) {
             active = false;  // first arrival: the partner will pair with it
@@ -657,41 +676,71 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
             cand = true;
           } else {
             slot = (slot + 1) & tmask;
-            if (++probes > tneed) { err_w |= kErrProbe; active = false; }
+            if (++probes > tneed) {
+              err_w |= kErrProbe;
+              active = false;
+            }
           }
         }
+        __threadfence();
         unsigned cm = __ballot_sync(0xffffffffu, cand);
         while (cm) {
-          const int L = __ffs(cm) - 1;
+          const int Ld = __ffs(cm) - 1;
           cm &= cm - 1;
-          const uint64_t pp = __shfl_sync(0xffffffffu, old, L) & 0x7fffffffull;
-          const int wjL = __shfl_sync(0xffffffffu, wj, L);
-          const uint64_t FwL = __shfl_sync(0xffffffffu, Fw, L);
-          const bool eq = warp_face_matches(st, sm, G, chunk, (long long)(pp / R), int(pp % R), e, S, s0, wjL, FwL,
-                                            nV, total, n);
-          if (lane == L) {
+          const uint64_t pp = __shfl_sync(0xffffffffu, old, Ld) & 0x7fffffffull;
+          const int wjL = __shfl_sync(0xffffffffu, wj, Ld);
+          const uint64_t FwL = __shfl_sync(0xffffffffu, Fw, Ld);
+          const bool eq =
+              warp_face_matches(st, (long long)(pp / R), int(pp % R), e, S, s0, wjL, FwL, nV, total, n);
+          if (lane == Ld) {
             if (eq) {
-              const uint64_t prev = atomicOr(reinterpret_cast<unsigned long long*>(st.table + slot),
+              const uint64_t prev = atomicOr(reinterpret_cast<unsigned long long*>(table + slot),
                                              (unsigned long long)kPaired);
               if (prev & kPaired) {
                 err_w |= kErrPairing;
               } else {
                 const int v2 = int(nV + (long long)(pp / R));
+                const bool m2 = ahead && __ldcg(Z + (long long)(i + 1) * Vcap + v2) < ZT(0);
+                const unsigned char nx = (m2 ? 1 : 0) | (m0n ? 2 : 0);
                 const int slot2 = atomicAdd(&sm.npairs, 1);
                 if (slot2 < kPairCap) {
                   sm.pairs[slot2] = make_int4(v2, v0, 0, 0);
+                  sm.pnext[slot2] = nx;
                 } else {
-                  const long long idx = atomic_add_ll(&cur->npairs, 1ll);
-                  st.EU[nE + total + idx] = v2;
-                  st.EW[nE + total + idx] = v0;
+                  const long long idx = nE + total + atomic_add_ll(&cur->npairs, 1ll);
+                  st.EU[idx] = v2;
+                  st.EW[idx] = v0;
+                  if (ahead && ((nx ^ (nx >> 1)) & 1)) {
+                    const long long b2 = atomic_add_ll(cnext, 1ll);
+                    lnext[b2] = (nx & 1) ? make_int4(int(idx), v0, v2, 0) : make_int4(int(idx), v2, v0, 0);
+                    set_flag(fnext, idx);
+                  }
                 }
               }
               active = false;
             } else {
               slot = (slot + 1) & tmask;
-              if (++probes > tneed) { err_w |= kErrProbe; active = false; }
+              if (++probes > tneed) {
+                err_w |= kErrProbe;
+                active = false;
+              }
             }
           }
+        }
+      }
+    }
+    // look-ahead: the two halves of the split edge at neuron i + 1
+    if (ahead && lane == 0) {
+      const bool mp = zpn < ZT(0), mq = zqn < ZT(0);
+      int4 ent[2];
+      int c = 0;
+      if (mp != m0n) ent[c++] = mp ? make_int4(ed, v0, p, 0) : make_int4(ed, p, v0, 0);
+      if (mq != m0n) ent[c++] = mq ? make_int4(int(nE + k), v0, q, 0) : make_int4(int(nE + k), q, v0, 0);
+      if (c) {
+        const long long b2 = atomic_add_ll(cnext, (long long)c);
+        for (int t2 = 0; t2 < c; ++t2) {
+          lnext[b2 + t2] = ent[t2];
+          set_flag(fnext, ent[t2].x);
         }
       }
     }
@@ -704,7 +753,7 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
     if (err_w) atomicOr(&st.g->error, err_w);
   }
   __syncthreads();
-  // this CTA's intersecting edges: one global allocation
+  // this CTA's intersecting edges: one global allocation, then their look-ahead
   const int np = sm.npairs < kPairCap ? sm.npairs : kPairCap;
   if (threadIdx.x == 0) {
     sm.acc[2] = np ? atomic_add_ll(&cur->npairs, (long long)np) : 0;
@@ -713,13 +762,56 @@ __device__ bool phase_split(const NetDesc& net, const State& st, int zb, int l, 
   }
   __syncthreads();
   const long long base = nE + total + sm.acc[2];
-  for (int t = threadIdx.x; t < np; t += kBlock) {
-    const int4 rec = sm.pairs[t];
-    st.EU[base + t] = rec.x;
-    st.EW[base + t] = rec.y;
-    if (st.deferred) st.vlist[base + t] = rec;
+  for (int t = threadIdx.x; t < ((np + 31) & ~31); t += kBlock) {
+    int4 ent[1];
+    int c = 0;
+    if (t < np) {
+      const int4 rec = sm.pairs[t];
+      st.EU[base + t] = rec.x;
+      st.EW[base + t] = rec.y;
+      if (st.deferred) st.vlist[base + t] = rec;
+      const unsigned char nx = sm.pnext[t];
+      if (ahead && ((nx ^ (nx >> 1)) & 1)) {
+        ent[0] = (nx & 1) ? make_int4(int(base + t), rec.y, rec.x, 0) : make_int4(int(base + t), rec.x, rec.y, 0);
+        c = 1;
+      }
+    }
+    if (ahead) warp_append(c, ent, lnext, fnext, cnext);
   }
+  // step (3) for the next neuron over the edges that did not split here
+  const ZT* znext = Z + (long long)(ahead ? i + 1 : 0) * Vcap;
+  scan_edges<ZT>(st, znext, nE, nV, st.flags[n & 1], ahead, lnext, fnext, cnext, n);
   return false;
+}
+
+// ---------------------------------------------------------------------------
+// Layer end: the codes of the layer's entries of every vertex from the signs
+// of its values (+ / - / 0 exactly on the folded hyperplane).
+template <typename ZT>
+__device__ void phase_pack(const NetDesc& net, const State& st, int l) {
+  const int H = net.w[l + 1];
+  const Counters* last = st.cnt + net.off[l] + H;
+  const long long nV = last->nV_before + last->nsplit;
+  if (nV < 0 || nV > st.Vcap) {
+    if (threadIdx.x == 0) report_corrupt(st.g, 12, l, nV, st.Vcap, 0);
+    return;
+  }
+  const long long Vcap = st.Vcap;
+  const ZT* Z = static_cast<const ZT*>(st.Z[l]);
+  const int e0 = net.m + net.off[l], wf = e0 >> 5, wl = (e0 + H - 1) >> 5;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nV; v += (long long)gridDim.x * blockDim.x) {
+    for (int w = wf; w <= wl; ++w) {
+      uint64_t word = w == wf ? (st.SIG[(long long)w * Vcap + v] & entries_below(w, e0)) : 0ull;
+      const int jb = 32 * w - e0 > 0 ? 32 * w - e0 : 0;
+      const int je = 32 * w + 32 - e0 < H ? 32 * w + 32 - e0 : H;
+      for (int j = jb; j < je; ++j) {
+        const ZT z = Z[(long long)j * Vcap + v];
+        const uint64_t code = z > ZT(0) ? kPlus : (z < ZT(0) ? kMinus : 0ull);
+        word |= code << (2 * ((e0 + j) & 31));
+      }
+      st.SIG[(long long)w * Vcap + v] = word;
+    }
+  }
 }
 
 }  // namespace pc

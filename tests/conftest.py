@@ -19,8 +19,10 @@ def pytest_configure(config):
 # GPU modules that run after all the others, in this order: rejected inputs,
 # the counting sweep (sixty extractions up to 5e6 edges), the polyhedral
 # domains, then the counting sweep at D = 5 and 6
+# and last of all the allocation-free entry point, so that a run that stops at
+# its first failure has run every other test before it
 _LAST = {"test_gpu_invalid_inputs.py": 1, "test_gpu_counting_sweep.py": 2, "test_gpu_domains.py": 3,
-         "test_gpu_counting_sweep_high_dims.py": 4}
+         "test_gpu_counting_sweep_high_dims.py": 4, "test_zz_no_alloc.py": 5}
 
 
 def pytest_collection_modifyitems(config, items):
