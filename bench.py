@@ -10,16 +10,18 @@ CUDA events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-The JSON line also carries the FP64 mode and the pruned (level-set)
-extraction on the same workload (`variants`), the serving measurement (`serving`: a Poisson stream of
-2000 extraction requests through the batched 8-slot server and the plain
-1-slot path; `--serve-requests 0` skips it), the counting sweep of Section
-5.1.2 (`counting_sweep`: vertex and edge counts, time and peak device memory
-of random four-hidden-layer nets of widths 10, 20, 40 for D = 1..5, five nets
-per point; `--sweep-dims ''` skips it), the same net on a simplex domain
-(`domain`; `--domain 0` skips it), the width-10 sweep nets for D = 6..10
-(`counting_sweep_w10`; `--sweep-dims-w10 ''` skips it), the roofline of the neuron loop, the
-clocks seen during the timed region and one oracle run on a host core.
+The JSON line (the last line on stdout) also carries the FP64 mode and the
+pruned (level-set) extraction on the same workload (`variants`), the
+rooflines of the neuron loop and of the tensor-core layer products on the
+D=5 width-40 counting-sweep net, where HBM can bind (`large`; `--large 0`
+skips it), and, last, the serving measurement (`serving`: a Poisson stream
+of 2000 extraction requests through the batched server and the plain 1-slot
+path; `--serve-requests 0` skips it).  Longer side measurements go to stderr,
+one JSON line each: the counting sweep of Section 5.1.2 (random
+four-hidden-layer nets of widths 10, 20, 40 for D = 1..5, five nets per
+point; `--sweep-dims ''` skips it), the same net on a simplex domain
+(`--domain 0` skips it) and the width-10 sweep nets for D = 6..10
+(`--sweep-dims-w10 ''` skips it).
 
 --impl reference times the FP64 CPU oracle as the reference arm
 on the host cores.  Under torchrun (N > 1) every rank runs an independent
@@ -40,10 +42,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) per k_layer launch, mixed precision, from one ncu
-# capture of this command (profiles/k_layer_torus_d3.md); set to None when
-# the kernel changes until it is captured again.
-K_LAYER_DRAM_BYTES_PER_LAUNCH = 105_200_000
+# DRAM bytes (read + write) per k_layer launch of the mixed-precision torus
+# extraction, from one ncu capture of the k_layer launches of one extraction,
+# and a hash of the kernel sources it was taken with: the figure is reported
+# only while the sources are unchanged (else traffic is null).
+K_LAYER_DRAM = {"bytes_per_launch": None, "sources_sha16": None}
+KERNEL_SOURCES = ("pc_phases.cuh", "pc_core.cu", "pc_device.cuh", "pc_newton.cuh")
 
 METRIC = "vertices+edges/s at D=3 (torus 3-64x4-1, box [-1,1]^3)"
 UNIT = "(V+E)/s"
@@ -116,17 +120,29 @@ class ClockSampler:
 
 # -- algorithmic bytes of the neuron loop -------------------------------------
 
-def neuron_loop_bytes(net, stats, precision: str) -> list:
-    """Bytes the per-neuron steps must move, per layer (one persistent launch each).
+def kernel_sources_sha16() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2306_07212_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
-    Per neuron step with V vertices, E edges, S splitting edges, K keys, P pairs:
-      sign   : V * (zb + 16)              z row read, sign word read+write
-      edges  : E * 8 + S * 4              endpoints read, splitting ids written
-      split  : S * (3 * (8D + H zb + 8W) + 28)   two endpoint records read, one
-               new record written (coordinates, H values, W sign words), split
-               id read, edge read and two edge writes
-      pairing: K * 16 + P * 8             hash slot write+read, new edge write
+
+def neuron_loop_bytes(net, stats, precision: str) -> list:
+    """Algorithmic bytes of the per-neuron steps, per layer (one k_layer launch each).
+
+    Per neuron step with V vertices, E edges, S splitting edges, K 2-face
+    keys and P paired faces (the per-neuron counters):
+      4 V                          the neuron's value row (zb bytes per value)
+      8 E                          every edge's two endpoints
+      S (3 (8D + zb H + 8W) + 16)  two endpoint records read and the new
+                                   vertex's written (coordinates, the layer's
+                                   H values, W sign words), 16 B of edges
+      24 K                         each key's 12-byte slot written and read
+      8 P                          each intersecting edge written
     zb = 4 (FP32 values) or 8 (FP64); W = 64-bit words per sign vector.
+    Sign-word gathers and error scales are not counted (cache-resident).
     """
     D = net.D
     zb = 8 if precision == "fp64" else 4
@@ -137,10 +153,51 @@ def neuron_loop_bytes(net, stats, precision: str) -> list:
         tot = 0
         for _ in range(H):
             V, E, S, K, P = (int(stats[n, k]) for k in (0, 1, 2, 3, 4))
-            tot += V * (zb + 16) + E * 8 + S * 4 + S * (3 * (8 * D + H * zb + 8 * W) + 28) + K * 16 + P * 8
+            tot += zb * V + 8 * E + S * (3 * (8 * D + H * zb + 8 * W) + 16) + 24 * K + 8 * P
             n += 1
         out.append(tot)
     return out
+
+
+def gemm_bytes_flops(net, stats, precision: str) -> list:
+    """Per layer l >= 1 (the tensor-core product): algorithmic bytes (read the
+    previous layer's values and the vertices' sign words, write this layer's
+    values) and useful flops 2 V H_{l-1} H_l, with V the vertices at the layer
+    start."""
+    zb = 8 if precision == "fp64" else 4
+    W = (2 * net.D + net.n_neurons + 31) // 32
+    out, off = [], 0
+    for l in range(net.L):
+        H, K = net.widths[l + 1], net.widths[l]
+        V = int(stats[off, 0])
+        out.append((zb * V * (K + H) + 8 * W * V, 2.0 * V * K * H))
+        off += H
+    return out
+
+
+def measure_tf32_tflops(device: int) -> float:
+    """Dense TF32 matmul rate of this GPU (torch.matmul, 8192^3, FP32 inputs
+    with TF32 tensor cores allowed), best of 5 after a warm-up."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        n = 8192
+        a = torch.randn(n, n, device=device)
+        b = torch.randn(n, n, device=device)
+        torch.matmul(a, b)
+        best = 0.0
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        del a, b
+        return round(best, 1)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
 # -- replicas: whole-job numbers --------------------------------------------
@@ -238,18 +295,16 @@ def run_ours(args, rank, world, local_rank):
     loop_avg = np.mean(np.stack(loop_ms), axis=0)  # per layer, ms
     gemm_avg = np.mean(np.stack(gemm_ms), axis=0)
     peak, peak_kind = _peaks()
-    achieved = sum(layer_bytes) / (loop_avg.sum() / 1e3) / 1e9
-    roofline = {"kernel": "k_layer (persistent neuron loop, one launch per layer)", "bound": "hbm",
-                "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                "traffic": K_LAYER_DRAM_BYTES_PER_LAUNCH if args.precision == "mixed" else None,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the k_layer launches of one "
-                                  "steady-state extraction of this workload (profiles/k_layer_torus_d3.md), "
-                                  "averaged per launch",
-                "bytes_per_launch_avg": int(sum(layer_bytes) / len(layer_bytes)),
-                "launch_ms_avg": round(float(loop_avg.mean()), 4),
-                "share_of_step": round(float(loop_avg.sum() / statistics.mean(step_ms)), 3),
-                "forward_product_ms_per_step": round(float(gemm_avg.sum()), 4)}
+    roofline = loop_roofline(layer_bytes, loop_avg, peak, peak_kind)
+    roofline["share_of_step"] = round(float(loop_avg.sum() / statistics.mean(step_ms)), 3)
+    roofline["forward_product_ms_per_step"] = round(float(gemm_avg.sum()), 4)
+    if args.precision == "mixed" and K_LAYER_DRAM["sources_sha16"] == kernel_sources_sha16():
+        roofline["traffic"] = K_LAYER_DRAM["bytes_per_launch"]
+        roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the k_layer launches of "
+                                      "one extraction of this workload, per launch")
+    else:
+        roofline["traffic"] = None
+        roofline["traffic_source"] = "not captured for these kernel sources"
     out = None
     if rank == 0:
         cpu = cpu_baseline(net, box) if world == 1 else None
@@ -270,70 +325,139 @@ def run_ours(args, rank, world, local_rank):
         if cpu:
             out["cpu_baseline"] = cpu
         if world == 1:
-            # the other precision modes on the same workload, same timing rules
-            # (reported beside the configured mixed-precision path)
             variants = {}
             runs = [(p, {"precision": p}) for p in ("fp64", "mixed") if p != args.precision]
-            # level-set extraction with pruning during subdivision (its V + E are the
-            # pruned complex's)
             runs.append(("prune", {"precision": args.precision, "prune": True}))
             for name, kw in runs:
                 try:
-                    with Extractor(device=local_rank, execution=args.execution, **kw) as vx:
-                        for _ in range(args.warmup):
-                            vx.extract(net, box, params=params_dev)
-                        vms = []
-                        for _ in range(args.steps):
-                            flush.zero_()
-                            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                            e0.record()
-                            vx.extract(net, box, params=params_dev)
-                            e1.record()
-                            e1.synchronize()
-                            vms.append(e0.elapsed_time(e1))
-                        vc = vx.counts()
-                        vunits = vc["nV"] + vc["nE"]
-                    variants[name] = {"value": round(vunits * len(vms) / (sum(vms) / 1e3), 1), "unit": UNIT,
-                                      "ms_per_step": round(sum(vms) / len(vms), 4), "steps": len(vms),
-                                      "n_vertices": vc["nV"], "n_edges": vc["nE"], **kw}
+                    variants[name] = time_variant(Extractor, local_rank, args, net, box, params_dev, flush, kw)
                 except Exception as exc:  # a variant never takes the main line down
-                    variants[name] = {"error": str(exc)[:300], **kw}
+                    variants[name] = {"error": str(exc)[:200], **kw}
             out["variants"] = variants
-        if args.serve_requests > 0 and world == 1:
-            lim = 1 << 30
-            serving = {
-                "workload": f"Poisson stream, mean 200 req/s, {args.serve_requests} requests, D in {{2,3,4}}, "
-                            "depth 2-6, width in {16,32,64,128}, He-normal FP32 weights, mixed precision; "
-                            f"requests estimated above {lim >> 30} GiB rejected"}
-            for name, slots in (("batched", 8), ("plain", 1)):
+            if args.large:
                 try:
-                    serving[name] = run_serving(args.serve_requests, slots, lim)
-                except Exception as exc:  # the extraction numbers above stand on their own
-                    serving[name] = {"slots": slots, "error": str(exc)[:300]}
-            out["serving"] = serving
-        if args.sweep_dims and world == 1:
-            try:
-                out["counting_sweep"] = run_counting_sweep(_dims(args.sweep_dims), args.sweep_seeds, local_rank,
-                                                           args.precision, args.execution)
-            except Exception as exc:  # the extraction numbers above stand on their own
-                out["counting_sweep"] = {"error": str(exc)[:300]}
-        if args.domain and world == 1:
-            try:
-                out["domain"] = run_domain(net, params_dev, flush, local_rank, args)
-            except Exception as exc:
-                out["domain"] = {"error": str(exc)[:300]}
-        if args.sweep_dims_w10 and world == 1:
-            # the width-10 nets further up in D (D > 8 on the PC_MAX_D=10 build)
-            try:
-                out["counting_sweep_w10"] = run_counting_sweep(_dims(args.sweep_dims_w10), args.sweep_seeds,
-                                                               local_rank, args.precision, args.execution,
-                                                               widths=(10,))
-            except Exception as exc:
-                out["counting_sweep_w10"] = {"error": str(exc)[:300]}
+                    out["large"] = run_large(local_rank, args, flush, peak, peak_kind)
+                except Exception as exc:
+                    out["large"] = {"error": str(exc)[:300]}
+        if args.serve_requests > 0 and world == 1:
+            out["serving"] = run_serving_pair(args)
+        # longer side measurements: one JSON line each on stderr, so that the
+        # main line (the last line on stdout) stays short
+        if world == 1:
+            extras = {}
+            if args.sweep_dims:
+                extras["counting_sweep"] = lambda: run_counting_sweep(_dims(args.sweep_dims), args.sweep_seeds,
+                                                                      local_rank, args.precision, args.execution)
+            if args.domain:
+                extras["domain"] = lambda: run_domain(net, params_dev, flush, local_rank, args)
+            if args.sweep_dims_w10:
+                extras["counting_sweep_w10"] = lambda: run_counting_sweep(
+                    _dims(args.sweep_dims_w10), args.sweep_seeds, local_rank, args.precision, args.execution,
+                    widths=(10,))
+            for name, fn in extras.items():
+                try:
+                    block = fn()
+                except Exception as exc:  # the main line stands on its own
+                    block = {"error": str(exc)[:300]}
+                print(json.dumps({"side_measurement": name, **block}), file=sys.stderr, flush=True)
     ex.close()
     if dist:
         dist.destroy_process_group()
     return out
+
+
+def loop_roofline(layer_bytes, loop_ms, peak, peak_kind) -> dict:
+    """HBM roofline of k_layer: algorithmic bytes per launch over the mean launch time."""
+    import numpy as np
+    achieved = sum(layer_bytes) / (float(np.sum(loop_ms)) / 1e3) / 1e9
+    return {"kernel": "k_layer (persistent neuron loop, one launch per layer)", "bound": "hbm",
+            "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "peak_source": peak_kind, "bytes_per_launch_avg": int(sum(layer_bytes) / len(layer_bytes)),
+            "launch_ms_avg": round(float(np.mean(loop_ms)), 4)}
+
+
+def time_variant(Extractor, device, args, net, box, params_dev, flush, kw, steps=None) -> dict:
+    import torch
+    steps = steps or args.steps
+    with Extractor(device=device, execution=args.execution, **kw) as vx:
+        for _ in range(args.warmup):
+            vx.extract(net, box, params=params_dev)
+        vms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            vx.extract(net, box, params=params_dev)
+            e1.record()
+            e1.synchronize()
+            vms.append(e0.elapsed_time(e1))
+        vc = vx.counts()
+    vunits = vc["nV"] + vc["nE"]
+    return {"value": round(vunits * len(vms) / (sum(vms) / 1e3), 1), "unit": UNIT,
+            "ms_per_step": round(sum(vms) / len(vms), 4), "steps": len(vms), "n_vertices": vc["nV"],
+            "n_edges": vc["nE"], **kw}
+
+
+def run_large(device: int, args, flush, peak, peak_kind) -> dict:
+    """The kernels where HBM can bind: the counting-sweep net D=5, width 40
+    (seed 0; 1.0e7 vertices, 4.8e7 edges), mixed precision.  Rooflines of
+    the neuron loop (bytes model above) and of the tensor-core layer
+    products (bytes, and useful flops against the measured TF32 rate)."""
+    import numpy as np
+    import torch
+    from paper_2306_07212_gb300 import Extractor, workloads
+    net, box = workloads.counting_sweep_net(5, 40, 0)
+    params = torch.from_numpy(net.flat_params()).cuda(device)
+    with Extractor(device=device, precision=args.precision, execution=args.execution, timers=True) as ex:
+        ex.extract(net, box, params=params)  # grows the buffers
+        step, loops, gemms = [], [], []
+        for _ in range(2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ex.extract(net, box, params=params)
+            e1.record()
+            e1.synchronize()
+            step.append(e0.elapsed_time(e1))
+            kt = ex.kernel_times_ms()
+            loops.append(kt[:, 1].copy())
+            gemms.append(kt[:, 0].copy())
+        c = ex.counts()
+        stats = ex.stats()
+        polish_ms = ex.polish_time_ms()
+    loop_ms = np.mean(np.stack(loops), axis=0)
+    gemm_ms = np.mean(np.stack(gemms), axis=0)
+    roof = loop_roofline(neuron_loop_bytes(net, stats, args.precision), loop_ms, peak, peak_kind)
+    tf32 = measure_tf32_tflops(device)
+    gb = gemm_bytes_flops(net, stats, args.precision)[1:]  # layers 2.. run on the tensor cores
+    gms = gemm_ms[1:]
+    gbytes = sum(b for b, _ in gb)
+    gflops = sum(f for _, f in gb)
+    gt = float(np.sum(gms)) / 1e3
+    return {"workload": "counting-sweep net D=5, MLP 5-40x4-1 (seed 0), box [-1,1]^5, one extraction",
+            "n_vertices": c["nV"], "n_edges": c["nE"], "ms": round(float(np.median(step)), 2),
+            "value": round((c["nV"] + c["nE"]) / (float(np.median(step)) / 1e3), 1), "unit": UNIT,
+            "loop_ms": round(float(np.sum(loop_ms)), 2), "forward_product_ms": round(float(np.sum(gemm_ms)), 2),
+            "polish_ms": round(polish_ms, 2), "roofline": roof,
+            "gemm_roofline": {"kernel": "k_gemm_tc (layers 2-5)", "bound": "hbm",
+                              "achieved": round(gbytes / gt / 1e9, 2), "peak": peak, "unit": "GB/s",
+                              "frac": round(gbytes / gt / 1e9 / peak, 4),
+                              "tensor_tflops": round(gflops / gt / 1e12, 2), "tf32_peak_tflops": tf32,
+                              "tensor_frac": round(gflops / gt / 1e12 / tf32, 4) if tf32 else None,
+                              "peak_source": "hbm " + peak_kind + "; TF32 measured in this run (torch.matmul 8192^3)"}}
+
+
+def run_serving_pair(args) -> dict:
+    """The serving workload through the batched server and the plain path."""
+    serving = {"workload": f"Poisson stream, mean 200 req/s, {args.serve_requests} requests, D in {{2,3,4}}, "
+                           "depth 2-6, width in {16,32,64,128}, He-normal FP32 weights, mixed precision; "
+                           f"requests estimated above {args.serve_max_gib} GiB rejected"}
+    for name, slots in (("batched", args.serve_slots), ("plain", 1)):
+        try:
+            serving[name] = run_serving(args.serve_requests, slots, int(args.serve_max_gib * (1 << 30)))
+        except Exception as exc:  # the extraction numbers above stand on their own
+            serving[name] = {"slots": slots, "error": str(exc)[:300]}
+    return serving
 
 
 def run_serving(n_requests: int, slots: int, request_max_bytes: int):
@@ -556,6 +680,11 @@ def main():
     ap.add_argument("--sweep-dims-w10", default="6-10",
                     help="input dimensions of the width-10 counting sweep beyond --sweep-dims ('' = skip it)")
     ap.add_argument("--domain", type=int, default=1, help="1: also time the net on a simplex domain")
+    ap.add_argument("--large", type=int, default=1,
+                    help="1: also the rooflines on the D=5, width-40 sweep net (1e7 vertices)")
+    ap.add_argument("--serve-slots", type=int, default=8, help="slots of the batched server")
+    ap.add_argument("--serve-max-gib", type=float, default=8.0,
+                    help="serving: requests whose memory estimate exceeds this are rejected")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

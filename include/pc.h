@@ -250,6 +250,29 @@ pc_status pc_backward(pc_ctx *ctx, const double *grad_x, double *grad_params, vo
  * PC_ERR_DEGENERATE on a non-generic cell).  Blocks until done. */
 pc_status pc_cell_counts(pc_ctx *ctx, int64_t *f_out, int n, int64_t *euler);
 
+/* The face poset of the last extraction's complex (Section 4.1: a k-cell
+ * has D - k zeros in its sign vector; perturbing one zero to + or - (a box
+ * facet's zero only to +, the inside) gives a (k+1)-cell that contains it,
+ * its parent).  Builds on the device, and keeps in the context until the
+ * next extraction: level 0 = the vertices (in pc_vertices order), level 1 =
+ * the edges (in pc_edges order), level k >= 2 = the k-cells by perturbation,
+ * deduplicated by 64-bit fingerprints with every duplicate compared word by
+ * word; and for every cell of level k < D its parents, the cells of level
+ * k + 1 obtained by perturbing its zeros in entry order, + before -.
+ * PC_ERR_PAIRING on a fingerprint collision or a vertex perturbation that is
+ * no edge, PC_ERR_DEGENERATE on a non-generic cell, PC_ERR_OOM.  Blocks. */
+pc_status pc_build_poset(pc_ctx *ctx);
+
+/* Level k of the poset (0 <= k <= D): *n_cells cells and *n_parents
+ * parent incidences (0 for k = D).  Non-null outputs are filled (host or
+ * device memory): cells, n_cells x S packed sign words, cell-major (cell i
+ * at cells + i * S, the code layout of pc_signvectors); for k < D the
+ * parents as CSR, row_ptr (n_cells + 1) and parents (n_parents indices into
+ * level k + 1).  PC_ERR_INVALID before pc_build_poset or after the next
+ * extraction. */
+pc_status pc_poset_level(pc_ctx *ctx, int k, int64_t *n_cells, int64_t *n_parents, uint64_t *cells,
+                         int64_t *row_ptr, int64_t *parents);
+
 /* Diagnostics of the last extraction, up to n int64 values: kernel launches
  * (cumulative over the context's life), capacity growths, polished vertices,
  * exact-zero pre-activations, FP64-undecidable signs, vertex / edge / hash

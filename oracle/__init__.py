@@ -77,6 +77,17 @@ def _load():
             lib.orc_faces.restype = ctypes.c_int64
             lib.orc_faces.argtypes = [vp, i64p]
             lib.orc_grad.argtypes = [vp, ctypes.c_int, i32p, f64p, f64p, f64p]
+            lib.orc_poset.restype = vp
+            lib.orc_poset.argtypes = [vp]
+            lib.orc_poset_status.argtypes = [vp]
+            lib.orc_poset_error.restype = ctypes.c_char_p
+            lib.orc_poset_error.argtypes = [vp]
+            for f in (lib.orc_poset_count, lib.orc_poset_nnz):
+                f.restype = ctypes.c_int64
+                f.argtypes = [vp, ctypes.c_int]
+            lib.orc_poset_cells.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int8)]
+            lib.orc_poset_incidence.argtypes = [vp, ctypes.c_int, i64p, i64p]
+            lib.orc_poset_free.argtypes = [vp]
             _lib = lib
     return _lib
 
@@ -212,6 +223,43 @@ def faces(res: Result):
     f = np.zeros(res.D + 1, np.int64)
     chi = lib.orc_faces(res._handle.h, _ptr(f, ctypes.c_int64))
     return f, int(chi)
+
+
+@dataclasses.dataclass
+class Poset:
+    """The face poset of an extracted complex (Section 4.1).  cells[k]: the
+    k-cells' sign vectors (n_k, m+N) int8, sorted lexicographically (-1 < 0
+    < +1); parents[k] (k < D): CSR (row_ptr (n_k + 1,), cols) of the
+    (k+1)-cells containing each k-cell, its zeros perturbed in entry order,
+    + before -.  status 0, or 5 when a perturbed vertex is not an edge."""
+
+    cells: list
+    parents: list
+    status: int
+    error: str
+
+
+def poset(res: Result) -> Poset:
+    lib = _load()
+    q = lib.orc_poset(res._handle.h)
+    try:
+        P = res.S.shape[1]
+        cells, parents = [], []
+        for k in range(res.D + 1):
+            n = lib.orc_poset_count(q, k)
+            c = np.empty((n, P), np.int8)
+            if n:
+                lib.orc_poset_cells(q, k, _ptr(c, ctypes.c_int8))
+            cells.append(c)
+            if k < res.D:
+                nnz = lib.orc_poset_nnz(q, k)
+                rp = np.empty(n + 1, np.int64)
+                cl = np.empty(max(nnz, 1), np.int64)
+                lib.orc_poset_incidence(q, k, _ptr(rp, ctypes.c_int64), _ptr(cl, ctypes.c_int64))
+                parents.append((rp, cl[:nnz]))
+        return Poset(cells, parents, lib.orc_poset_status(q), lib.orc_poset_error(q).decode())
+    finally:
+        lib.orc_poset_free(q)
 
 
 def grad(net, res: Result, gx: np.ndarray) -> np.ndarray:

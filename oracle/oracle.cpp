@@ -13,6 +13,9 @@
 //                 repeated for every neuron of every layer.
 //   orc_faces     k-cell counts by repeated perturbation (Section 4.1), used
 //                 for the Euler-characteristic check.
+//   orc_poset     the face poset itself (Section 4.1): every level's cells
+//                 and, for each cell, the cells one level up that contain it
+//                 (its parents), by perturbing each of its zeros.
 //   orc_brute     the complex from its definition (Section 3.3-3.4): every
 //                 D-subset of {box facets, neuron zero sets} under every
 //                 activation pattern, plus edges by a midpoint test.
@@ -55,6 +58,13 @@
 //   orc_faces     the region count of clipped generic arrangements (1 + the
 //                 k-subsets whose flat meets the open domain, by a linear
 //                 program per flat) and Euler characteristic 1.
+//   orc_poset     the perturbed vertices against the independently built
+//                 edges; the face relation of polyhedral complexes: every
+//                 interval of length two is a diamond (exactly two cells in
+//                 between), the boundary of every k-cell is a (k-1)-sphere
+//                 (its faces' Euler characteristic is 1 - (-1)^k); and the
+//                 geometry: the centroid of a cell's vertices, evaluated by a
+//                 forward pass, has the cell's sign vector.
 //   orc_brute     the definition itself; it agrees with orc_extract and
 //                 with the closed forms above.
 //   orc_grad      central finite differences of FP64 extractions.
@@ -382,6 +392,88 @@ void subdivide(const Net& net, int max_neurons, Result& R, bool prune) {
 }
 
 // ---- k-cells by perturbation (Section 4.1) ---------------------------------
+
+// The face poset: level 0 the vertices' sign vectors, level 1 the edges' (the
+// join of their two vertices), level k >= 2 every perturbation of a zero of a
+// (k-1)-cell (a box facet's zero only toward +, the inside); each level sorted
+// (entries compared as -1 < 0 < +1).  The incidence of level k < D lists for
+// each k-cell the (k+1)-cells that contain it: its zeros perturbed one at a
+// time in entry order, + before -.  A perturbation of a vertex that is not an
+// edge fails the poset (status 5): the vertices' perturbations are checked
+// against the edges built from the extraction.
+struct Poset {
+  int D = 0, P = 0;
+  std::vector<std::vector<std::vector<int8_t>>> cells;
+  std::vector<std::vector<int64_t>> row_ptr, cols;
+  int status = 0;
+  std::string err;
+};
+
+Poset* build_poset(const Result& R) {
+  auto* Q = new Poset;
+  const int D = R.D, m = R.m, P = R.P;
+  Q->D = D;
+  Q->P = P;
+  Q->cells.resize(D + 1);
+  std::set<std::vector<int8_t>> lev;
+  for (int64_t v = 0; v < R.nV(); ++v)
+    lev.insert(std::vector<int8_t>(R.S.begin() + v * P, R.S.begin() + (v + 1) * P));
+  Q->cells[0].assign(lev.begin(), lev.end());
+  lev.clear();
+  for (auto& ed : R.E) {
+    std::vector<int8_t> s(P);
+    for (int j = 0; j < P; ++j) {
+      const int8_t a = R.S[size_t(ed[0]) * P + j], b = R.S[size_t(ed[1]) * P + j];
+      s[j] = a != 0 ? a : b;
+    }
+    lev.insert(s);
+  }
+  if (D >= 1) Q->cells[1].assign(lev.begin(), lev.end());
+  for (int k = 2; k <= D; ++k) {
+    lev.clear();
+    for (auto& c : Q->cells[k - 1]) {
+      std::vector<int8_t> s = c;
+      for (int j = 0; j < P; ++j) {
+        if (c[j] != 0) continue;
+        for (int sg = 1; sg >= -1; sg -= 2) {
+          if (j < m && sg < 0) continue;
+          s[j] = int8_t(sg);
+          lev.insert(s);
+          s[j] = 0;
+        }
+      }
+    }
+    Q->cells[k].assign(lev.begin(), lev.end());
+  }
+  Q->row_ptr.resize(D);
+  Q->cols.resize(D);
+  for (int k = 0; k < D; ++k) {
+    const auto& up = Q->cells[k + 1];
+    auto& rp = Q->row_ptr[k];
+    auto& cl = Q->cols[k];
+    rp.assign(1, 0);
+    for (auto& c : Q->cells[k]) {
+      std::vector<int8_t> s = c;
+      for (int j = 0; j < P; ++j) {
+        if (c[j] != 0) continue;
+        for (int sg = 1; sg >= -1; sg -= 2) {
+          if (j < m && sg < 0) continue;
+          s[j] = int8_t(sg);
+          const auto it = std::lower_bound(up.begin(), up.end(), s);
+          if (it == up.end() || *it != s) {
+            Q->status = 5;
+            Q->err = "a perturbation of a " + std::to_string(k) + "-cell is not a " + std::to_string(k + 1) + "-cell";
+          } else {
+            cl.push_back(int64_t(it - up.begin()));
+          }
+          s[j] = 0;
+        }
+      }
+      rp.push_back(int64_t(cl.size()));
+    }
+  }
+  return Q;
+}
 
 int64_t faces(const Result& R, int64_t* f_out) {
   const int D = R.D, m = R.m, P = R.P;
@@ -802,6 +894,25 @@ void orc_stats(void* r, int64_t* out) {
 
 // f_out has D+1 entries (f_0 .. f_D); returns the Euler characteristic.
 int64_t orc_faces(void* r, int64_t* f_out) { return faces(*static_cast<Result*>(r), f_out); }
+
+// The face poset of an extraction (build_poset); free with orc_poset_free.
+void* orc_poset(void* r) { return build_poset(*static_cast<Result*>(r)); }
+int orc_poset_status(void* q) { return static_cast<Poset*>(q)->status; }
+const char* orc_poset_error(void* q) { return static_cast<Poset*>(q)->err.c_str(); }
+int64_t orc_poset_count(void* q, int k) { return int64_t(static_cast<Poset*>(q)->cells[k].size()); }
+// n_k x P sign vectors of level k, sorted
+void orc_poset_cells(void* q, int k, int8_t* out) {
+  auto* Q = static_cast<Poset*>(q);
+  for (size_t i = 0; i < Q->cells[k].size(); ++i) std::memcpy(out + i * Q->P, Q->cells[k][i].data(), Q->P);
+}
+// parents of level k (k < D) as CSR: row_ptr (n_k + 1), cols (nnz)
+int64_t orc_poset_nnz(void* q, int k) { return int64_t(static_cast<Poset*>(q)->cols[k].size()); }
+void orc_poset_incidence(void* q, int k, int64_t* row_ptr, int64_t* cols) {
+  auto* Q = static_cast<Poset*>(q);
+  std::memcpy(row_ptr, Q->row_ptr[k].data(), Q->row_ptr[k].size() * sizeof(int64_t));
+  std::memcpy(cols, Q->cols[k].data(), Q->cols[k].size() * sizeof(int64_t));
+}
+void orc_poset_free(void* q) { delete static_cast<Poset*>(q); }
 
 int orc_grad(void* r, int L, const int32_t* widths, const double* params, const double* gx,
              double* dtheta) {

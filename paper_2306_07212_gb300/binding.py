@@ -31,7 +31,8 @@ EXPORTS = ["pc_default_options", "pc_create", "pc_destroy", "pc_set_allocator", 
            "pc_diagnostics", "pc_kernel_times", "pc_error_estimates", "pc_values", "pc_extract_noalloc",
            "pc_estimate_bytes", "pc_server_default_options", "pc_server_create", "pc_server_submit",
            "pc_server_poll", "pc_server_error", "pc_server_wait_all", "pc_server_outputs", "pc_server_release", "pc_server_stats",
-           "pc_server_destroy", "pc_last_error", "pc_cell_counts", "pc_extract_domain", "pc_check_domain"]
+           "pc_server_destroy", "pc_last_error", "pc_cell_counts", "pc_extract_domain", "pc_check_domain",
+           "pc_build_poset", "pc_poset_level"]
 
 
 class PcError(RuntimeError):
@@ -112,6 +113,8 @@ def load_library(path: str = LIB):
                                            ctypes.c_int64, ctypes.c_int64, i64p, i64p, vp]
         lib.pc_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         lib.pc_cell_counts.argtypes = [vp, i64p, ctypes.c_int, i64p]
+        lib.pc_build_poset.argtypes = [vp]
+        lib.pc_poset_level.argtypes = [vp, ctypes.c_int, i64p, i64p, vp, vp, vp]
         lib.pc_extract_domain.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp, ctypes.c_int64, vp,
                                           ctypes.c_int64, vp, vp]
         lib.pc_check_domain.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int64, vp, ctypes.c_int64, vp]
@@ -369,6 +372,23 @@ class Extractor:
         self._check(self._lib.pc_cell_counts(self._ctx, f.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), D + 1,
                                              ctypes.byref(chi)))
         return f, int(chi.value)
+
+    def poset(self):
+        """pc_build_poset then pc_poset_level for every level: a list over k
+        = 0..D of (cells (n_k, S) uint64 packed sign words, row_ptr, parents),
+        the CSR of the level-(k+1) cells containing each k-cell (None for k = D)."""
+        self._check(self._lib.pc_build_poset(self._ctx))
+        D, S = self.counts()["D"], self.counts()["S"]
+        out = []
+        for k in range(D + 1):
+            n, nnz = ctypes.c_int64(), ctypes.c_int64()
+            self._check(self._lib.pc_poset_level(self._ctx, k, ctypes.byref(n), ctypes.byref(nnz), None, None, None))
+            cells = np.empty((n.value, S), np.uint64)
+            rp = np.empty(n.value + 1, np.int64) if k < D else None
+            cols = np.empty(max(nnz.value, 1), np.int64) if k < D else None
+            self._check(self._lib.pc_poset_level(self._ctx, k, None, None, _addr(cells), _addr(rp), _addr(cols)))
+            out.append((cells, rp, cols[:nnz.value] if cols is not None else None))
+        return out
 
     def vertices_into(self, out) -> None:
         """Copies the D x nV coordinate block into `out` (host or device memory)."""

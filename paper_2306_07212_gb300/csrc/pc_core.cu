@@ -273,8 +273,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_decide(NetDesc net, State st, int
 
 template <typename ZT>
 __global__ void __launch_bounds__(kBlock) k_scan0(NetDesc net, State st, int l) {
+  __shared__ Smem sm;
   if (cta_stopped(st)) return;
-  phase_scan0<ZT>(net, st, l);
+  phase_scan0<ZT>(net, st, l, sm);
 }
 
 template <typename ZT, bool MIXED>
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_layer(NetDesc net, State st, int 
     phase_decide<ZT, MIXED>(net, st, l, sm, dsm, mw);
     if (!grid_barrier(st.g, passed)) return;  // uniform per CTA
     if (cta_stopped(st)) return;
-    phase_scan0<ZT>(net, st, l);
+    phase_scan0<ZT>(net, st, l, sm);
     if (!grid_barrier(st.g, passed)) return;
     if (cta_stopped(st)) return;
   }
@@ -647,19 +648,23 @@ struct Kernels {
                                           c->res_smem, c->stream));
       c->launches += 1;
     } else {
+      // grids sized to the edge capacity (2048 edges per CTA of a scan
+      // iteration), so that the small extractions of concurrent requests
+      // share the GPU; every phase is written for any grid size
+      const int gs = int(std::max<long long>(8, std::min<long long>(c->grid_step, c->Ecap / 2048)));
       if (prologue) {
-        k_decide<ZT, MIXED><<<c->grid_step, kBlock, c->res_smem, c->stream>>>(c->net, st, l, c->mw);
+        k_decide<ZT, MIXED><<<gs, kBlock, c->res_smem, c->stream>>>(c->net, st, l, c->mw);
         PC_CUDA(cudaGetLastError());
-        k_scan0<ZT><<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l);
+        k_scan0<ZT><<<gs, kBlock, 0, c->stream>>>(c->net, st, l);
         PC_CUDA(cudaGetLastError());
         c->launches += 2;
       }
       for (int i = i_begin; i < H; ++i) {
-        k_step<ZT, MIXED><<<c->grid_step, kBlock, c->res_smem, c->stream>>>(c->net, st, l, i, c->mw);
+        k_step<ZT, MIXED><<<gs, kBlock, c->res_smem, c->stream>>>(c->net, st, l, i, c->mw);
         PC_CUDA(cudaGetLastError());
         c->launches += 1;
       }
-      k_pack<ZT><<<c->grid_step, kBlock, 0, c->stream>>>(c->net, st, l);
+      k_pack<ZT><<<gs, kBlock, 0, c->stream>>>(c->net, st, l);
       PC_CUDA(cudaGetLastError());
       c->launches += 1;
     }
@@ -1162,6 +1167,7 @@ pc_status pc_destroy(pc_ctx* c) {
   ctx_free(c, c->cnt);
   ctx_free(c, c->g);
   ctx_free(c, c->dom_buf);
+  pc_poset_release(c);
   c->release_extra();
   cudaStreamSynchronize(c->stream);
   for (auto& e : c->ev) {
@@ -1188,6 +1194,7 @@ pc_status pc_extract(pc_ctx* c, int L, const int32_t* widths, const double* para
   if (!c || !widths || !params || !lo || !hi) return PC_ERR_INVALID;
   c->err.clear();
   c->have_result = false;
+  pc_poset_release(c);
   try {
     PC_CUDA(cudaSetDevice(c->device));
     c->stream = static_cast<cudaStream_t>(stream);
@@ -1224,6 +1231,7 @@ pc_status pc_extract_domain(pc_ctx* c, int L, const int32_t* widths, const doubl
   if (!c || !widths || !params || L < 1) return PC_ERR_INVALID;
   c->err.clear();
   c->have_result = false;
+  pc_poset_release(c);
   const DomainIn dom{m, A, cvec, nv0, X0, ne0, E0};
   double lo[kMaxD], hi[kMaxD];
   const std::string why = check_domain(widths[0], dom, lo, hi);

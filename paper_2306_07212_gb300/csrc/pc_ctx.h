@@ -7,6 +7,7 @@
 #include <stdexcept>
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "pc.h"
 #include "pc_device.cuh"
@@ -19,6 +20,9 @@ pc::State pc_make_state(pc_ctx* c);
 
 // canonical output order (pc_canon.cu)
 void pc_canonicalize(pc_ctx* c);
+
+// face poset (pc_cells.cu)
+void pc_poset_release(pc_ctx* c);
 
 // pruning during subdivision (pc_prune.cu)
 void pc_prune_edges(pc_ctx* c, const pc::State& st, int l);
@@ -113,6 +117,16 @@ struct pc_ctx {
   cudaEvent_t ev[2 * pc::kMaxL + 1][2] = {};
   int ev_used[2 * pc::kMaxL + 1] = {};
   double ktime_ms[2 * pc::kMaxL + 1] = {};
+
+  // face poset of the last result (pc_build_poset): per level the cells
+  // (cell-major sign words) and below D the parents as CSR
+  std::vector<void*> poset_bufs;
+  void* poset_cells[pc::kMaxD + 1] = {};
+  long long poset_n[pc::kMaxD + 1] = {};
+  void* poset_rp[pc::kMaxD] = {};
+  void* poset_cols[pc::kMaxD] = {};
+  long long poset_nnz[pc::kMaxD] = {};
+  int poset_levels = 0;
 
   // adjoint scratch (allocated lazily by pc_backward)
   void* adj[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

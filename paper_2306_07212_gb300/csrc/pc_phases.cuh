@@ -38,15 +38,22 @@
 
 namespace pc {
 
-constexpr int kPairCap = 1024;         // intersecting edges a CTA buffers per step
+constexpr int kPairCap = 1024;         // intersecting edges a CTA buffers before it appends them
+constexpr int kLaCap = 512;            // look-ahead list entries a CTA buffers
 constexpr int kPendCap = 2 * kBlock;   // vertices a CTA queues for an FP64 re-decision
 
 struct Smem {
   long long pend[kPendCap];
   int4 pairs[kPairCap];                // (v_a, v_b, zero ordinals, neuron + 1)
   unsigned char pnext[kPairCap];       // bit 0: v_a is - at the next neuron, bit 1: v_b is -
+  int4 la[kLaCap];                     // split halves that split again at the next neuron
   int npairs;
+  int npairla;                         // buffered pairs that split at the next neuron
+  int nla;
+  int cursor;
   int npend;
+  int wcnt[kWarps];
+  long long pbase, lbase, sbase;
   int zlist[kWarps][16];
   int nzl[kMaxD + 2];
   NewtonOut nout;
@@ -161,7 +168,7 @@ __device__ void drain_pending(const NetDesc& net, const State& st, int l, int e_
 // Layer start, step (2) for every current vertex and every neuron of the
 // layer (values from the layer-start product, step (1)).
 template <typename ZT, bool MIXED>
-__device__ void phase_decide(const NetDesc& net, const State& st, int l, Smem& sm, double* ws, int mw) {
+__device__ __noinline__ void phase_decide(const NetDesc& net, const State& st, int l, Smem& sm, double* ws, int mw) {
   const int n0 = net.off[l], H = net.w[l + 1];
   long long nV, nE;
   if (!step_counts(st, n0, nV, nE)) {
@@ -206,46 +213,67 @@ __device__ void phase_decide(const NetDesc& net, const State& st, int l, Smem& s
 // Step (3) for one neuron over the edges [0, nE): an edge splits iff its
 // endpoints' values in zrow have opposite signs.  Edges flagged in fcur are
 // skipped (they split in the current step, whose warps classify their
-// halves); fcur is cleared on the way.  classify = false only clears.
-template <typename ZT>
-__device__ void scan_edges(const State& st, const ZT* zrow, long long nE, long long nV, uint32_t* fcur,
-                           bool classify, int4* lnext, uint32_t* fnext, long long* counter, int n) {
-  const int lane = threadIdx.x & 31;
-  const long long W = (long long)gridDim.x * kWarps;
-  for (long long tile = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); tile * 128 < nE; tile += W) {
-    const long long idx0 = tile * 128 + 4 * lane;
-    uint32_t skip = 0;
-    if (fcur != nullptr) {
-      const uint32_t fw = idx0 < nE ? fcur[idx0 >> 5] : 0u;
-      skip = (fw >> (idx0 & 31)) & 0xFu;
-      __syncwarp();
-      if ((lane & 7) == 0 && idx0 < nE && fw) fcur[idx0 >> 5] = 0u;
-    }
-    if (!classify) continue;
-    int4 eu = make_int4(0, 0, 0, 0), ew = make_int4(0, 0, 0, 0);
-    int nvalid = 0;
-    if (idx0 < nE) {
-      nvalid = nE - idx0 >= 4 ? 4 : int(nE - idx0);
-      if (nvalid == 4) {
-        eu = *reinterpret_cast<const int4*>(st.EU + idx0);
-        ew = *reinterpret_cast<const int4*>(st.EW + idx0);
-      } else {
-        int* pu = &eu.x;
-        int* pw = &ew.x;
-        for (int q = 0; q < nvalid; ++q) {
-          pu[q] = st.EU[idx0 + q];
-          pw[q] = st.EW[idx0 + q];
-        }
+// halves); fcur is cleared on the way.  classify = false only clears.  A CTA
+// takes 2048 consecutive edges per iteration (one 128-edge tile per warp,
+// CTAs round-robin) and reserves its list entries with one atomic.
+// The flag word and the four edges (endpoint pairs) of one lane of a tile.
+struct ScanTile {
+  uint32_t fw;
+  int4 eu, ew;
+  int nvalid;
+};
+
+__device__ __forceinline__ ScanTile scan_load(const State& st, const uint32_t* fcur, long long idx0, long long nE,
+                                              bool classify) {
+  ScanTile T;
+  T.fw = (fcur != nullptr && idx0 < nE) ? fcur[idx0 >> 5] : 0u;
+  T.eu = make_int4(0, 0, 0, 0);
+  T.ew = make_int4(0, 0, 0, 0);
+  T.nvalid = 0;
+  if (classify && idx0 < nE) {
+    T.nvalid = nE - idx0 >= 4 ? 4 : int(nE - idx0);
+    if (T.nvalid == 4) {
+      T.eu = *reinterpret_cast<const int4*>(st.EU + idx0);
+      T.ew = *reinterpret_cast<const int4*>(st.EW + idx0);
+    } else {
+      int* pu = &T.eu.x;
+      int* pw = &T.ew.x;
+      for (int q = 0; q < T.nvalid; ++q) {
+        pu[q] = st.EU[idx0 + q];
+        pw[q] = st.EW[idx0 + q];
       }
     }
-    const int* pu = &eu.x;
-    const int* pw = &ew.x;
+  }
+  return T;
+}
+
+template <typename ZT>
+__device__ void scan_edges(const State& st, const ZT* zrow, long long nE, long long nV, uint32_t* fcur,
+                           bool classify, int4* lnext, uint32_t* fnext, long long* counter, int n, Smem& sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long G = gridDim.x;
+  constexpr long long kSpan = 4ll * kBlock;
+  const long long iters = (nE + kSpan * G - 1) / (kSpan * G);
+  // the next iteration's flags and endpoints are loaded while this one is classified
+  ScanTile nxt = scan_load(st, fcur, blockIdx.x * kSpan + warp * 128 + 4 * lane, nE, classify);
+  for (long long it = 0; it < iters; ++it) {
+    const long long idx0 = (it * G + blockIdx.x) * kSpan + warp * 128 + 4 * lane;
+    const ScanTile T = nxt;
+    if (it + 1 < iters) nxt = scan_load(st, fcur, idx0 + kSpan * G, nE, classify);
+    const uint32_t skip = (T.fw >> (idx0 & 31)) & 0xFu;
+    if (fcur != nullptr) {
+      __syncwarp();
+      if ((lane & 7) == 0 && idx0 < nE && T.fw) fcur[idx0 >> 5] = 0u;
+    }
+    if (!classify) continue;  // uniform
+    const int* pu = &T.eu.x;
+    const int* pw = &T.ew.x;
     int4 ent[4];
     int c = 0;
     uint32_t nib = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      if (q >= nvalid || ((skip >> q) & 1u)) continue;
+      if (q >= T.nvalid || ((skip >> q) & 1u)) continue;
       const int u = pu[q], w = pw[q];
       if (u < 0 || u >= nV || w < 0 || w >= nV) {
         report_corrupt(st.g, 6, n, idx0 + q, u, w);  // never index with it
@@ -262,12 +290,22 @@ __device__ void scan_edges(const State& st, const ZT* zrow, long long nE, long l
       const int y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    const int tot = __shfl_sync(0xffffffffu, x, 31);
-    if (tot == 0) continue;
-    long long base = 0;
-    if (lane == 31) base = atomic_add_ll(counter, (long long)tot);
-    base = __shfl_sync(0xffffffffu, base, 31) + (x - c);
-    for (int t = 0; t < c; ++t) lnext[base + t] = ent[t];
+    if (lane == 31) sm.wcnt[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long tot = 0;
+      for (int w = 0; w < kWarps; ++w) {
+        const int cw = sm.wcnt[w];
+        sm.wcnt[w] = int(tot);
+        tot += cw;
+      }
+      sm.sbase = tot ? atomic_add_ll(counter, tot) : 0;
+    }
+    __syncthreads();
+    if (c) {
+      const long long base = sm.sbase + sm.wcnt[warp] + (x - c);
+      for (int t = 0; t < c; ++t) lnext[base + t] = ent[t];
+    }
     uint32_t word = nib << (idx0 & 31);  // the 8 lanes of a flag word OR their nibbles
     word |= __shfl_xor_sync(0xffffffffu, word, 1);
     word |= __shfl_xor_sync(0xffffffffu, word, 2);
@@ -278,7 +316,7 @@ __device__ void scan_edges(const State& st, const ZT* zrow, long long nE, long l
 
 // Layer start, step (3) for neuron 0 of layer l.
 template <typename ZT>
-__device__ void phase_scan0(const NetDesc& net, const State& st, int l) {
+__device__ void phase_scan0(const NetDesc& net, const State& st, int l, Smem& sm) {
   const int n0 = net.off[l];
   long long nV, nE;
   if (!step_counts(st, n0, nV, nE)) {
@@ -286,7 +324,7 @@ __device__ void phase_scan0(const NetDesc& net, const State& st, int l) {
     return;
   }
   const ZT* zrow = static_cast<const ZT*>(st.Z[l]);
-  scan_edges<ZT>(st, zrow, nE, nV, nullptr, true, st.list[n0 & 1], st.flags[n0 & 1], &st.cnt[n0 + 1].nsplit, n0);
+  scan_edges<ZT>(st, zrow, nE, nV, nullptr, true, st.list[n0 & 1], st.flags[n0 & 1], &st.cnt[n0 + 1].nsplit, n0, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -333,6 +371,46 @@ __device__ __forceinline__ bool warp_face_matches(const State& st, long long k2,
 }
 
 // ---------------------------------------------------------------------------
+// Appends the CTA's buffered intersecting edges (and those of them that split
+// at the next neuron) and buffered look-ahead entries: one atomic each for
+// the CTA.  All threads call it after a __syncthreads.
+__device__ void flush_cta(const State& st, Counters* cur, long long* cnext, int4* lnext, uint32_t* fnext,
+                          long long ebase, bool ahead, Smem& sm) {
+  const int np = sm.npairs, nla = sm.nla, npla = sm.npairla;
+  if (threadIdx.x == 0) {
+    sm.pbase = np ? atomic_add_ll(&cur->npairs, (long long)np) : 0;
+    sm.lbase = (ahead && nla + npla) ? atomic_add_ll(cnext, (long long)(nla + npla)) : 0;
+    sm.cursor = 0;
+  }
+  __syncthreads();
+  const long long pb = ebase + sm.pbase;
+  for (int t = threadIdx.x; t < np; t += kBlock) {
+    const int4 rec = sm.pairs[t];
+    st.EU[pb + t] = rec.x;
+    st.EW[pb + t] = rec.y;
+    if (st.deferred) st.vlist[pb + t] = rec;
+    const unsigned char nx = sm.pnext[t];
+    if (ahead && ((nx ^ (nx >> 1)) & 1)) {  // the new edge splits at the next neuron
+      const int j = atomicAdd(&sm.cursor, 1);
+      lnext[sm.lbase + nla + j] = (nx & 1) ? make_int4(int(pb + t), rec.y, rec.x, 0)
+                                           : make_int4(int(pb + t), rec.x, rec.y, 0);
+      set_flag(fnext, pb + t);
+    }
+  }
+  for (int t = threadIdx.x; t < nla; t += kBlock) {
+    const int4 ent = sm.la[t];
+    lnext[sm.lbase + t] = ent;
+    set_flag(fnext, ent.x);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sm.npairs = 0;
+    sm.nla = 0;
+    sm.npairla = 0;
+  }
+  __syncthreads();
+}
+
 // One neuron step: steps (4)+(5) for the listed splitting edges, step (3) for
 // the next neuron.  Returns true when the step must not run (capacity ran out
 // -- nothing has been written -- or a counter is corrupt); the caller exits.
@@ -342,6 +420,12 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
   const int n = net.off[l] + i;
   const int H = net.w[l + 1];
   const bool ahead = i + 1 < H;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long G = gridDim.x;
+  const int4* lcur = st.list[n & 1];
+  // this warp's first splitting edge, loaded together with the counters
+  const long long k_first = (long long)warp * G + blockIdx.x;
+  const int4 sg_first = k_first < st.Ecap ? lcur[k_first] : make_int4(-1, -1, -1, 0);
   Counters* cur = st.cnt + n + 1;
   long long nV, nE;
   if (!step_counts(st, n, nV, nE)) {
@@ -383,6 +467,8 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
   }
   if (threadIdx.x == 0) {
     sm.npairs = 0;
+    sm.npairla = 0;
+    sm.nla = 0;
     sm.npend = 0;
     sm.acc[0] = sm.acc[1] = 0;
   }
@@ -390,16 +476,13 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
   {
     uint64_t* told = st.table + (long long)((n + 1) & 1) * 2 * st.Tcap;
     const long long tprev = 2 * st.cnt[n].tsize;
-    for (long long t = (long long)blockIdx.x * kBlock + threadIdx.x; t < tprev; t += (long long)gridDim.x * kBlock)
-      told[t] = kEmpty;
+    for (long long t = (long long)blockIdx.x * kBlock + threadIdx.x; t < tprev; t += G * kBlock) told[t] = kEmpty;
   }
   __syncthreads();
   const long long Vcap = st.Vcap;
   ZT* Z = static_cast<ZT*>(st.Z[l]);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int e = m + n;
   const int e0 = m + net.off[l];
-  const int4* lcur = st.list[n & 1];
   int4* lnext = st.list[(n + 1) & 1];
   uint32_t* fnext = st.flags[(n + 1) & 1];
   long long* cnext = ahead ? &st.cnt[n + 2].nsplit : nullptr;
@@ -409,11 +492,14 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
   int* zlist = sm.zlist[warp];
   long long nkeys_w = 0, ndeg_w = 0;
   int err_w = 0;
-  const long long G = gridDim.x;
+  unsigned long long paired_seen = 0;  // paired flags found by this lane's second arrivals
   const long long Wt = G * kWarps;
   const long long rounds = (total + Wt - 1) / Wt;
+  int4 sg_next = sg_first;
   for (long long rd = 0; rd < rounds; ++rd) {
-    const long long k = rd * Wt + (long long)warp * G + blockIdx.x;  // splits dealt over the CTAs first
+    const long long k = rd * Wt + k_first;  // splits dealt over the CTAs first
+    const int4 sg_this = sg_next;
+    if (k + Wt < total) sg_next = lcur[k + Wt];  // the next round's, loaded during this one
     // ---- part A: the new vertex (step (4)) ----
     bool okA = false, pend = false, bad = false;
     int32_t ed = 0, p = 0, q = 0;
@@ -421,7 +507,7 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
     uint64_t s0 = 0, zm = 0;
     ZT zpn = ZT(0), zqn = ZT(0), z0n = ZT(0);  // values at neuron i + 1
     if (k < total) {
-      const int4 sg = lcur[k];
+      const int4 sg = sg_this;
       ed = sg.x;
       p = sg.y;  // V+
       q = sg.z;  // V-
@@ -429,6 +515,7 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
       if (!okA && lane == 0) report_corrupt(st.g, 4, n, ed, p, q);
     }
     if (okA) {
+      // every load of the endpoints is issued before any of them is used
       const ZT za0 = Z[(long long)i * Vcap + p], zb0 = Z[(long long)i * Vcap + q];
       double xp = 0.0, xq = 0.0;
       if (lane < D) {
@@ -439,6 +526,13 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
       if (lane < S) {
         sp = st.SIG[(long long)lane * Vcap + p];
         sq = st.SIG[(long long)lane * Vcap + q];
+      }
+      ZT zp0[2], zq0[2];  // rows lane, lane + 32 of the first 64
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int j = 32 * hh + lane;
+        zp0[hh] = j < H ? Z[(long long)j * Vcap + p] : ZT(0);
+        zq0[hh] = j < H ? Z[(long long)j * Vcap + q] : ZT(0);
       }
       float rp = 0.f, rq = 0.f, xep = 0.f, xeq = 0.f;
       if (TRACK && lane == 0) {
@@ -459,22 +553,23 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
       const ZT tz = static_cast<ZT>(t);
       // earlier layers' entries: the join of the endpoints' words
       const uint64_t below = lane < S ? entries_below(lane, e0) : 0ull;
-      uint64_t conf = ((sp & kEvenBits) & ((sq >> 1) & kEvenBits)) | ((sq & kEvenBits) & ((sp >> 1) & kEvenBits));
+      const uint64_t conf = ((sp & kEvenBits) & ((sq >> 1) & kEvenBits)) | ((sq & kEvenBits) & ((sp >> 1) & kEvenBits));
       if (conf & below) err_w |= kErrConflict;
       s0 = (sp | sq) & below;
       float amax = 0.f;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (64 * c >= H) continue;  // warp-uniform
+      float zk[2] = {0.f, 0.f};  // this lane's new values of rows lane, lane + 32 (filter)
+      for (int c = 0; 64 * c < H; ++c) {
         uint32_t plus2[2], minus2[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int j = 64 * c + 32 * h + lane;
-          ZT zp = ZT(0), zq = ZT(0), zj = ZT(0);
+        for (int hh = 0; hh < 2; ++hh) {
+          const int j = 64 * c + 32 * hh + lane;
+          ZT zp = zp0[hh], zq = zq0[hh], zj = ZT(0);
+          if (c > 0) {
+            zp = j < H ? Z[(long long)j * Vcap + p] : ZT(0);
+            zq = j < H ? Z[(long long)j * Vcap + q] : ZT(0);
+          }
           bool pl = false, mi = false;
           if (j < H) {
-            zp = Z[(long long)j * Vcap + p];
-            zq = Z[(long long)j * Vcap + q];
             if (j < i) {  // processed: the join of the endpoints' signs, value made consistent
               pl = zp > ZT(0) || zq > ZT(0);
               mi = zp < ZT(0) || zq < ZT(0);
@@ -493,9 +588,10 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
             Z[(long long)j * Vcap + v0] = zj;  // row i: exactly 0
             if (TRACK) amax = fmaxf(amax, fabsf(static_cast<float>(zj)) * nrl[3 * j + 2]);
           }
-          plus2[h] = __ballot_sync(0xffffffffu, pl);
-          minus2[h] = __ballot_sync(0xffffffffu, mi);
-          if (ahead && 64 * c + 32 * h <= i + 1 && i + 1 < 64 * c + 32 * h + 32) {  // warp-uniform
+          if (c == 0) zk[hh] = static_cast<float>(zj);
+          plus2[hh] = __ballot_sync(0xffffffffu, pl);
+          minus2[hh] = __ballot_sync(0xffffffffu, mi);
+          if (ahead && 64 * c + 32 * hh <= i + 1 && i + 1 < 64 * c + 32 * hh + 32) {  // warp-uniform
             const int src = (i + 1) & 31;
             zpn = __shfl_sync(0xffffffffu, zp, src);
             zqn = __shfl_sync(0xffffffffu, zq, src);
@@ -504,12 +600,12 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
         }
         // this chunk's codes (entries e0 + 64c ...) into the lane's word
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint64_t il = spread_even(plus2[h]) | (spread_even(minus2[h]) << 1);
+        for (int hh = 0; hh < 2; ++hh) {
+          const uint64_t il = spread_even(plus2[hh]) | (spread_even(minus2[hh]) << 1);
           if (!il) continue;
-          const int ent = e0 + 64 * c + 32 * h, w = ent >> 5, s = 2 * (ent & 31);
-          if (lane == w) s0 |= il << s;
-          if (s && lane == w + 1) s0 |= il >> (64 - s);
+          const int ent = e0 + 64 * c + 32 * hh, w = ent >> 5, sft = 2 * (ent & 31);
+          if (lane == w) s0 |= il << sft;
+          if (sft && lane == w + 1) s0 |= il >> (64 - sft);
         }
       }
       if (TRACK) {
@@ -532,13 +628,14 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
           const float xe = fmaxf(xep, xeq);
           st.exc[v0] = sqrtf(xe * xe + shift * shift);
         }
-        if (MIXED) {  // this lane's new values of the later neurons, as it wrote them
+        if (MIXED) {  // the later neurons' new values within the filter
           esc0 = __shfl_sync(0xffffffffu, esc0, 0);
           bool f = false;
-          for (int j = lane; j < H; j += 32)
-            if (j > i)
-              f = f || fabsf(static_cast<float>(Z[(long long)j * Vcap + v0])) <=
-                           net.kappa * (nrl[3 * j] * esc0 + 2.9802322e-8f * nrl[3 * j + 1]);
+          for (int j = lane; j < H; j += 32) {
+            if (j <= i) continue;
+            const float zv = j < 64 ? zk[j >> 5] : static_cast<float>(Z[(long long)j * Vcap + v0]);
+            f = f || fabsf(zv) <= net.kappa * (nrl[3 * j] * esc0 + 2.9802322e-8f * nrl[3 * j + 1]);
+          }
           pend = __any_sync(0xffffffffu, f);
         }
       }
@@ -564,160 +661,101 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
       __syncthreads();
       if (sm.npend > 0) drain_pending<ZT>(net, st, l, e + 1, i + 1, mw, ws, sm);
     }
-    if (!okA) continue;
-    // ---- part B: the parent 2-faces (step (5)) and the look-ahead ----
-    if (ahead && pend) z0n = Z[(long long)(i + 1) * Vcap + v0];  // re-decided by this CTA
-    const bool m0n = z0n < ZT(0);
-    const int c0 = __popcll(zm);
-    int x = c0;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    const int nz = __shfl_sync(0xffffffffu, x, 31);
-    {
-      int kk = x - c0;
-      uint64_t mm = zm;
-      while (mm) {
-        const int bit = __ffsll((long long)mm) - 1;
-        if (kk < 16) zlist[kk] = lane * 32 + bit / 2;
-        ++kk;
-        mm &= mm - 1;
+    if (okA) {
+      // ---- part B: the parent 2-faces (step (5)) and the look-ahead ----
+      if (ahead && pend) z0n = Z[(long long)(i + 1) * Vcap + v0];  // re-decided by this CTA
+      const bool m0n = z0n < ZT(0);
+      const int c0 = __popcll(zm);
+      int x = c0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
       }
-    }
-    uint64_t hb = lane < S ? word_hash(lane, s0) : 0ull;
-    for (int o = 16; o > 0; o >>= 1) hb ^= __shfl_xor_sync(0xffffffffu, hb, o);
-    __syncwarp();
-    if (nz != D - 1) bad = true;
-    // this lane's key: zero ordinal lane / 2, sign + (even lane) or - (odd)
-    const int o = lane >> 1;
-    const bool minus = lane & 1;
-    const int jz = (nz == D - 1 && o < nz) ? zlist[o] : 0;
-    const int wj = jz >> 5, shj = 2 * (jz & 31);
-    const uint64_t s0w = __shfl_sync(0xffffffffu, s0, wj);
-    const bool has_key = (nz == D - 1) && (o < nz) && !(minus && jz < m);
-    nkeys_w += __popc(__ballot_sync(0xffffffffu, has_key));
-    if (bad) ndeg_w += (lane == 0);
-    uint64_t Fw = 0, h = 0;
-    long long slot = 0;
-    if (has_key) {
-      Fw = (s0w & ~(3ull << shj)) | ((minus ? kMinus : kPlus) << shj);
-      h = hb ^ word_hash(wj, s0w) ^ word_hash(wj, Fw);
-      slot = (long long)(h & (uint64_t)tmask);
-    }
-    if (st.deferred) {
-      // Full 64-bit fingerprint and payload in one 16-byte slot: the first
-      // arrival inserts both with one 128-bit CAS, the second finds the
-      // partner (and its sign at the next neuron, bit 62) in the same atomic
-      // and pairs at once.  Every pairing is re-checked exactly after the
-      // extraction (k_verify_pairs) from the two new vertices' sign vectors.
+      const int nz = __shfl_sync(0xffffffffu, x, 31);
+      {
+        int kk = x - c0;
+        uint64_t mm = zm;
+        while (mm) {
+          const int bit = __ffsll((long long)mm) - 1;
+          if (kk < 16) zlist[kk] = lane * 32 + bit / 2;
+          ++kk;
+          mm &= mm - 1;
+        }
+      }
+      uint64_t hb = lane < S ? word_hash(lane, s0) : 0ull;
+      for (int o = 16; o > 0; o >>= 1) hb ^= __shfl_xor_sync(0xffffffffu, hb, o);
+      __syncwarp();
+      if (nz != D - 1) bad = true;
+      // this lane's key: zero ordinal lane / 2, sign + (even lane) or - (odd)
+      const int o = lane >> 1;
+      const bool minus = lane & 1;
+      const int jz = (nz == D - 1 && o < nz) ? zlist[o] : 0;
+      const int wj = jz >> 5, shj = 2 * (jz & 31);
+      const uint64_t s0w = __shfl_sync(0xffffffffu, s0, wj);
+      const bool has_key = (nz == D - 1) && (o < nz) && !(minus && jz < m);
+      nkeys_w += __popc(__ballot_sync(0xffffffffu, has_key));
+      if (bad) ndeg_w += (lane == 0);
+      uint64_t Fw = 0, h = 0;
+      long long slot = 0;
       if (has_key) {
-        if (h == kEmpty) h = kEmpty - 1;
-        const unsigned long long mine = (uint64_t(k) * R + uint64_t(lane)) | (m0n ? (1ull << 62) : 0ull);
-        unsigned long long* tb = reinterpret_cast<unsigned long long*>(table);
-        for (long long probes = 0;; ++probes) {
-          if (probes > tneed) {
-            err_w |= kErrProbe;
-            break;
-          }
-          unsigned long long ok, ov;
-          cas128(tb + 2 * slot, kEmpty, kEmpty, h, mine, ok, ov);
-          if (ok == kEmpty) break;  // first arrival
-          if (ok == h) {
-            const unsigned long long prev = atomicOr(tb + 2 * slot + 1, kPaired64);
-            if (prev & kPaired64) {
-              err_w |= kErrPairing;
-            } else {
+        Fw = (s0w & ~(3ull << shj)) | ((minus ? kMinus : kPlus) << shj);
+        h = hb ^ word_hash(wj, s0w) ^ word_hash(wj, Fw);
+        slot = (long long)(h & (uint64_t)tmask);
+      }
+      if (st.deferred) {
+        // Full 64-bit fingerprint and payload in one 16-byte slot: the first
+        // arrival inserts both with one 128-bit CAS, the second finds the
+        // partner (and its sign at the next neuron, bit 62) in the same
+        // atomic and pairs at once; the paired flag it sets is checked at the
+        // end.  Every pairing is re-checked exactly after the extraction
+        // (k_verify_pairs) from the two new vertices' sign vectors.
+        if (has_key) {
+          if (h == kEmpty) h = kEmpty - 1;
+          const unsigned long long mine = (uint64_t(k) * R + uint64_t(lane)) | (m0n ? (1ull << 62) : 0ull);
+          unsigned long long* tb = reinterpret_cast<unsigned long long*>(table);
+          for (long long probes = 0;; ++probes) {
+            if (probes > tneed) {
+              err_w |= kErrProbe;
+              break;
+            }
+            unsigned long long ok, ov;
+            cas128(tb + 2 * slot, kEmpty, kEmpty, h, mine, ok, ov);
+            if (ok == kEmpty) break;  // first arrival
+            if (ok == h) {
+              paired_seen |= atomicOr(tb + 2 * slot + 1, kPaired64);
               const unsigned long long pay = ov & ~(kPaired64 | (1ull << 62));
               const long long k2 = (long long)(pay / R);
               const int r2 = int(pay % R);
-              const int4 rec = make_int4(int(nV + k2), v0, (r2 << 16) | lane, n + 1);
               const unsigned char nx = ((ov >> 62) & 1ull ? 1 : 0) | (m0n ? 2 : 0);
-              const int slot2 = atomicAdd(&sm.npairs, 1);
-              if (slot2 < kPairCap) {
-                sm.pairs[slot2] = rec;
-                sm.pnext[slot2] = nx;
-              } else {
-                const long long idx = nE + total + atomic_add_ll(&cur->npairs, 1ll);
-                st.EU[idx] = rec.x;
-                st.EW[idx] = rec.y;
-                st.vlist[idx] = rec;
-                if (ahead && ((nx ^ (nx >> 1)) & 1)) {
-                  const long long b2 = atomic_add_ll(cnext, 1ll);
-                  lnext[b2] = (nx & 1) ? make_int4(int(idx), rec.y, rec.x, 0) : make_int4(int(idx), rec.x, rec.y, 0);
-                  set_flag(fnext, idx);
-                }
-              }
+              const int slot2 = atomicAdd(&sm.npairs, 1);  // < kPairCap: flushed every round
+              sm.pairs[slot2] = make_int4(int(nV + k2), v0, (r2 << 16) | lane, n + 1);
+              sm.pnext[slot2] = nx;
+              if (ahead && ((nx ^ (nx >> 1)) & 1)) atomicAdd(&sm.npairla, 1);
+              break;
             }
-            break;
-          }
-          slot = (slot + 1) & tmask;
-        }
-      }
-    } else {
-      // Inline: a 32-bit tag; the second arrival compares the full faces
-      // before it pairs.  The partner's sign words and value at the next
-      // neuron are read from memory, so they are fenced before the insert.
-      __threadfence();
-      __syncwarp();
-      const uint32_t tag = uint32_t(h >> 32);
-      const uint64_t mine = has_key ? ((uint64_t(tag) << 32) | (uint64_t(k) * R + uint64_t(lane))) : 0ull;
-      bool active = has_key;
-      long long probes = 0;
-      while (__any_sync(0xffffffffu, active)) {
-        bool cand = false;
-        uint64_t old = 0;
-        if (active) {
-          old = atomicCAS(reinterpret_cast<unsigned long long*>(table + slot), (unsigned long long)kEmpty,
-                          (unsigned long long)mine);
-          if (old == kEmpty) {
-            active = false;  // first arrival: the partner will pair with it
-          } else if (uint32_t(old >> 32) == tag) {
-            cand = true;
-          } else {
             slot = (slot + 1) & tmask;
-            if (++probes > tneed) {
-              err_w |= kErrProbe;
-              active = false;
-            }
           }
         }
+      } else {
+        // Inline: a 32-bit tag; the second arrival compares the full faces
+        // before it pairs.  The partner's sign words and value at the next
+        // neuron are read from memory, so they are fenced before the insert.
         __threadfence();
-        unsigned cm = __ballot_sync(0xffffffffu, cand);
-        while (cm) {
-          const int Ld = __ffs(cm) - 1;
-          cm &= cm - 1;
-          const uint64_t pp = __shfl_sync(0xffffffffu, old, Ld) & 0x7fffffffull;
-          const int wjL = __shfl_sync(0xffffffffu, wj, Ld);
-          const uint64_t FwL = __shfl_sync(0xffffffffu, Fw, Ld);
-          const bool eq =
-              warp_face_matches(st, (long long)(pp / R), int(pp % R), e, S, s0, wjL, FwL, nV, total, n);
-          if (lane == Ld) {
-            if (eq) {
-              const uint64_t prev = atomicOr(reinterpret_cast<unsigned long long*>(table + slot),
-                                             (unsigned long long)kPaired);
-              if (prev & kPaired) {
-                err_w |= kErrPairing;
-              } else {
-                const int v2 = int(nV + (long long)(pp / R));
-                const bool m2 = ahead && __ldcg(Z + (long long)(i + 1) * Vcap + v2) < ZT(0);
-                const unsigned char nx = (m2 ? 1 : 0) | (m0n ? 2 : 0);
-                const int slot2 = atomicAdd(&sm.npairs, 1);
-                if (slot2 < kPairCap) {
-                  sm.pairs[slot2] = make_int4(v2, v0, 0, 0);
-                  sm.pnext[slot2] = nx;
-                } else {
-                  const long long idx = nE + total + atomic_add_ll(&cur->npairs, 1ll);
-                  st.EU[idx] = v2;
-                  st.EW[idx] = v0;
-                  if (ahead && ((nx ^ (nx >> 1)) & 1)) {
-                    const long long b2 = atomic_add_ll(cnext, 1ll);
-                    lnext[b2] = (nx & 1) ? make_int4(int(idx), v0, v2, 0) : make_int4(int(idx), v2, v0, 0);
-                    set_flag(fnext, idx);
-                  }
-                }
-              }
-              active = false;
+        __syncwarp();
+        const uint32_t tag = uint32_t(h >> 32);
+        const uint64_t mine = has_key ? ((uint64_t(tag) << 32) | (uint64_t(k) * R + uint64_t(lane))) : 0ull;
+        bool active = has_key;
+        long long probes = 0;
+        while (__any_sync(0xffffffffu, active)) {
+          bool cand = false;
+          uint64_t old = 0;
+          if (active) {
+            old = atomicCAS(reinterpret_cast<unsigned long long*>(table + slot), (unsigned long long)kEmpty,
+                            (unsigned long long)mine);
+            if (old == kEmpty) {
+              active = false;  // first arrival: the partner will pair with it
+            } else if (uint32_t(old >> 32) == tag) {
+              cand = true;
             } else {
               slot = (slot + 1) & tmask;
               if (++probes > tneed) {
@@ -726,26 +764,63 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
               }
             }
           }
+          __threadfence();
+          unsigned cm = __ballot_sync(0xffffffffu, cand);
+          while (cm) {
+            const int Ld = __ffs(cm) - 1;
+            cm &= cm - 1;
+            const uint64_t pp = __shfl_sync(0xffffffffu, old, Ld) & 0x7fffffffull;
+            const int wjL = __shfl_sync(0xffffffffu, wj, Ld);
+            const uint64_t FwL = __shfl_sync(0xffffffffu, Fw, Ld);
+            const bool eq =
+                warp_face_matches(st, (long long)(pp / R), int(pp % R), e, S, s0, wjL, FwL, nV, total, n);
+            if (lane == Ld) {
+              if (eq) {
+                const uint64_t prev = atomicOr(reinterpret_cast<unsigned long long*>(table + slot),
+                                               (unsigned long long)kPaired);
+                if (prev & kPaired) {
+                  err_w |= kErrPairing;
+                } else {
+                  const int v2 = int(nV + (long long)(pp / R));
+                  const bool m2 = ahead && __ldcg(Z + (long long)(i + 1) * Vcap + v2) < ZT(0);
+                  const unsigned char nx = (m2 ? 1 : 0) | (m0n ? 2 : 0);
+                  const int slot2 = atomicAdd(&sm.npairs, 1);  // < kPairCap: flushed every round
+                  sm.pairs[slot2] = make_int4(v2, v0, 0, 0);
+                  sm.pnext[slot2] = nx;
+                  if (ahead && ((nx ^ (nx >> 1)) & 1)) atomicAdd(&sm.npairla, 1);
+                }
+                active = false;
+              } else {
+                slot = (slot + 1) & tmask;
+                if (++probes > tneed) {
+                  err_w |= kErrProbe;
+                  active = false;
+                }
+              }
+            }
+          }
         }
       }
-    }
-    // look-ahead: the two halves of the split edge at neuron i + 1
-    if (ahead && lane == 0) {
-      const bool mp = zpn < ZT(0), mq = zqn < ZT(0);
-      int4 ent[2];
-      int c = 0;
-      if (mp != m0n) ent[c++] = mp ? make_int4(ed, v0, p, 0) : make_int4(ed, p, v0, 0);
-      if (mq != m0n) ent[c++] = mq ? make_int4(int(nE + k), v0, q, 0) : make_int4(int(nE + k), q, v0, 0);
-      if (c) {
-        const long long b2 = atomic_add_ll(cnext, (long long)c);
-        for (int t2 = 0; t2 < c; ++t2) {
-          lnext[b2 + t2] = ent[t2];
-          set_flag(fnext, ent[t2].x);
+      // look-ahead: the two halves of the split edge at neuron i + 1
+      if (ahead && lane == 0) {
+        const bool mp = zpn < ZT(0), mq = zqn < ZT(0);
+        int4 ent[2];
+        int c = 0;
+        if (mp != m0n) ent[c++] = mp ? make_int4(ed, v0, p, 0) : make_int4(ed, p, v0, 0);
+        if (mq != m0n) ent[c++] = mq ? make_int4(int(nE + k), v0, q, 0) : make_int4(int(nE + k), q, v0, 0);
+        if (c) {
+          const int b2 = atomicAdd(&sm.nla, c);  // < kLaCap: flushed every round
+          for (int t2 = 0; t2 < c; ++t2) sm.la[b2 + t2] = ent[t2];
         }
       }
+      __syncwarp();
     }
-    __syncwarp();
+    // keep the CTA's buffers from filling up in the next round
+    __syncthreads();
+    if (sm.npairs > kPairCap - kWarps * R || sm.nla > kLaCap - 2 * kWarps)
+      flush_cta(st, cur, cnext, lnext, fnext, nE + total, ahead, sm);
   }
+  if (paired_seen & kPaired64) err_w |= kErrPairing;  // a third arrival at a 2-face
   err_w = __reduce_or_sync(0xffffffffu, err_w);
   if (lane == 0) {
     if (nkeys_w) atomicAdd(reinterpret_cast<unsigned long long*>(&sm.acc[0]), (unsigned long long)nkeys_w);
@@ -753,34 +828,14 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
     if (err_w) atomicOr(&st.g->error, err_w);
   }
   __syncthreads();
-  // this CTA's intersecting edges: one global allocation, then their look-ahead
-  const int np = sm.npairs < kPairCap ? sm.npairs : kPairCap;
   if (threadIdx.x == 0) {
-    sm.acc[2] = np ? atomic_add_ll(&cur->npairs, (long long)np) : 0;
     if (sm.acc[0]) atomic_add_ll(&cur->nkeys, sm.acc[0]);
     if (sm.acc[1]) atomic_add_ll(&cur->ndegenerate, sm.acc[1]);
   }
-  __syncthreads();
-  const long long base = nE + total + sm.acc[2];
-  for (int t = threadIdx.x; t < ((np + 31) & ~31); t += kBlock) {
-    int4 ent[1];
-    int c = 0;
-    if (t < np) {
-      const int4 rec = sm.pairs[t];
-      st.EU[base + t] = rec.x;
-      st.EW[base + t] = rec.y;
-      if (st.deferred) st.vlist[base + t] = rec;
-      const unsigned char nx = sm.pnext[t];
-      if (ahead && ((nx ^ (nx >> 1)) & 1)) {
-        ent[0] = (nx & 1) ? make_int4(int(base + t), rec.y, rec.x, 0) : make_int4(int(base + t), rec.x, rec.y, 0);
-        c = 1;
-      }
-    }
-    if (ahead) warp_append(c, ent, lnext, fnext, cnext);
-  }
+  if (sm.npairs || sm.nla) flush_cta(st, cur, cnext, lnext, fnext, nE + total, ahead, sm);
   // step (3) for the next neuron over the edges that did not split here
   const ZT* znext = Z + (long long)(ahead ? i + 1 : 0) * Vcap;
-  scan_edges<ZT>(st, znext, nE, nV, st.flags[n & 1], ahead, lnext, fnext, cnext, n);
+  scan_edges<ZT>(st, znext, nE, nV, st.flags[n & 1], ahead, lnext, fnext, cnext, n, sm);
   return false;
 }
 
@@ -788,7 +843,7 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
 // Layer end: the codes of the layer's entries of every vertex from the signs
 // of its values (+ / - / 0 exactly on the folded hyperplane).
 template <typename ZT>
-__device__ void phase_pack(const NetDesc& net, const State& st, int l) {
+__device__ __noinline__ void phase_pack(const NetDesc& net, const State& st, int l) {
   const int H = net.w[l + 1];
   const Counters* last = st.cnt + net.off[l] + H;
   const long long nV = last->nV_before + last->nsplit;

@@ -149,8 +149,9 @@ int64_t pc_estimate_bytes(int L, const int32_t* widths) {
   const double E = D * V + double(D << (D - 1));
   const double S = std::ceil((2.0 * D + N) / 32.0);
   // per vertex: coordinates, two value buffers (float), error estimates, signs;
-  // per edge: endpoints and the staged split record; plus the hash table
-  const double bytes = V * (8.0 * D + 2 * 4.0 * hmax + 8 + 8.0 * S) + E * (8 + 16) + 8.0 * 2 * E;
+  // per edge: endpoints, two 16-byte splitting-edge lists, the pairing record
+  // and two flag bits; two hash tables of about E / 2 16-byte slots each
+  const double bytes = V * (8.0 * D + 2 * 4.0 * hmax + 8 + 8.0 * S) + E * (8 + 32 + 16 + 0.25) + 16.0 * E;
   // capacity growth doubles buffers: budget for the worst case of 2x
   const double total = 2.0 * bytes + 64.0 * 1024 * 1024;
   return total > 9.0e18 ? INT64_MAX : int64_t(total);

@@ -172,3 +172,35 @@ def test_zero_residual_sees_every_chunk():
     assert bench.zero_residual(net, box, X, words) < 1e-13
     X[-1] += 1e-4  # a vertex in the last chunk moved off its zero set
     assert bench.zero_residual(net, box, X, words) > 1e-6
+
+
+def test_neuron_loop_bytes_follow_the_per_step_model():
+    """4 V + 8 E + S (3 (8D + 4H + 8W) + 16) + 24 K + 8 P per step (FP32
+    values), summed per layer; FP64 values count 8 bytes each."""
+    import numpy as np
+    from paper_2306_07212_gb300 import workloads as wl
+    net = wl.he_normal_mlp([3, 2, 1], seed=0)  # two layers: H = 2, then 1
+    stats = np.array([[10, 20, 3, 8, 4, 0, 0, 0],
+                      [13, 27, 1, 4, 2, 0, 0, 0],
+                      [14, 30, 2, 6, 3, 0, 0, 0]], np.int64)
+    W = (2 * 3 + 3 + 31) // 32
+    step = lambda V, E, S, K, P, H, zb: zb * V + 8 * E + S * (3 * (8 * 3 + H * zb + 8 * W) + 16) + 24 * K + 8 * P
+    got = bench.neuron_loop_bytes(net, stats, "mixed")
+    assert got == [step(10, 20, 3, 8, 4, 2, 4) + step(13, 27, 1, 4, 2, 2, 4), step(14, 30, 2, 6, 3, 1, 4)]
+    got64 = bench.neuron_loop_bytes(net, stats, "fp64")
+    assert got64[1] == step(14, 30, 2, 6, 3, 1, 8)
+    gb = bench.gemm_bytes_flops(net, stats, "mixed")
+    assert gb[0] == (4 * 10 * (3 + 2) + 8 * W * 10, 2.0 * 10 * 3 * 2)
+    assert gb[1] == (4 * 14 * (2 + 1) + 8 * W * 14, 2.0 * 14 * 2 * 1)
+
+
+def test_loop_roofline_arithmetic():
+    r = bench.loop_roofline([2e9, 4e9], [1.0, 3.0], 6000.0, "measured")
+    assert r["achieved"] == round(6e9 / 4e-3 / 1e9, 2) and r["bound"] == "hbm"
+    assert r["frac"] == round(r["achieved"] / 6000.0, 4) and r["launch_ms_avg"] == 2.0
+
+
+def test_traffic_is_tied_to_the_kernel_sources():
+    sha = bench.kernel_sources_sha16()
+    assert len(sha) == 16 and all(ch in "0123456789abcdef" for ch in sha)
+    assert sha == bench.kernel_sources_sha16()
