@@ -465,7 +465,7 @@ def run_serving(n_requests: int, slots: int, request_max_bytes: int):
     import numpy as np
     from paper_2306_07212_gb300 import binding, workloads
     reqs = workloads.serving_stream(n_requests)
-    with binding.Server(max_slots=slots, request_max_bytes=request_max_bytes, mem_budget_bytes=48 << 30) as srv:
+    with binding.Server(max_slots=slots, request_max_bytes=request_max_bytes, mem_budget_bytes=160 << 30) as srv:
         t0 = time.perf_counter()
         ids = []
         for r in reqs:
@@ -683,7 +683,7 @@ def main():
     ap.add_argument("--large", type=int, default=1,
                     help="1: also the rooflines on the D=5, width-40 sweep net (1e7 vertices)")
     ap.add_argument("--serve-slots", type=int, default=8, help="slots of the batched server")
-    ap.add_argument("--serve-max-gib", type=float, default=8.0,
+    ap.add_argument("--serve-max-gib", type=float, default=64.0,
                     help="serving: requests whose memory estimate exceeds this are rejected")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))

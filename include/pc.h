@@ -328,8 +328,9 @@ typedef struct {
  * generic ReLU nets with N neurons (the measured range is 0.4 - 1.2), edges ~
  * D x vertices, doubled for capacity growth.  -1 on bad input. */
 int64_t pc_estimate_bytes(int L, const int32_t *widths);
-/* Defaults: 8 slots, mixed precision, stepwise execution, no polish, 64 GiB
- * budget, 8 GiB per request. */
+/* Defaults: 8 slots, mixed precision, stepwise execution, no polish, 160 GiB
+ * budget, 64 GiB per request.  A slot whose context holds more than 8 GiB
+ * after a request frees its buffers (the next request allocates again). */
 void pc_server_default_options(pc_server_options *opt);
 pc_status pc_server_create(pc_server **out, int device, const pc_server_options *opt);
 /* Inputs are host arrays (copied): widths L+1, params flat float64, box D. */

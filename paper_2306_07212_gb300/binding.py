@@ -404,8 +404,8 @@ class Server:
     poll or wait for their results (latencies on the server's clock)."""
 
     def __init__(self, device: int = 0, max_slots: int = 8, precision: str = "mixed", execution: str = "stepwise",
-                 polish: int = 0, keep_outputs: bool = False, mem_budget_bytes: int = 64 << 30,
-                 request_max_bytes: int = 8 << 30):
+                 polish: int = 0, keep_outputs: bool = False, mem_budget_bytes: int = 160 << 30,
+                 request_max_bytes: int = 64 << 30):
         self._lib = load_library()
         o = ServerOptions()
         self._lib.pc_server_default_options(ctypes.byref(o))

@@ -1071,6 +1071,16 @@ void StateBufs::release(pc_ctx* c) {
   ctx_free(c, tape_t);
 }
 
+void pc_release_buffers(pc_ctx* c) {
+  cudaSetDevice(c->device);
+  c->bufs.release(c);
+  c->Vcap = c->Ecap = c->Tcap = 0;
+  c->shape_D = c->shape_S = c->shape_H = 0;
+  c->have_result = false;
+  pc_poset_release(c);
+  cudaStreamSynchronize(c->stream);
+}
+
 // Dynamic shared-memory limits of the kernels, set to constant maxima so that
 // every context (in any thread) agrees; a per-network value would race.
 void pc_adjoint_set_attributes();

@@ -29,6 +29,10 @@
 
 #include "pc.h"
 
+// Frees a context's extraction buffers (pc_core.cu); the next extraction
+// allocates them again.
+void pc_release_buffers(pc_ctx* c);
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -48,6 +52,9 @@ struct Request {
 };
 
 }  // namespace
+
+// Device bytes a slot's context may keep between requests.
+constexpr int64_t kTrimBytes = int64_t(8) << 30;
 
 struct pc_server {
   int device = 0;
@@ -116,6 +123,13 @@ void pc_server::worker(int slot) {
       }
     }
     if (st != PC_OK) r->err = ctx ? pc_last_error(ctx) : "context creation failed";
+    // a slot that grew large for this request gives its buffers back, so
+    // that idle slots do not hold memory the admission budget does not see
+    if (ctx) {
+      int64_t d[10] = {0};
+      pc_diagnostics(ctx, d, 10);
+      if (d[8] > kTrimBytes) pc_release_buffers(ctx);
+    }
     {
       std::lock_guard<std::mutex> lk(mu);
       r->res.status = st;
@@ -164,8 +178,8 @@ void pc_server_default_options(pc_server_options* o) {
   o->precision = PC_PREC_MIXED;
   o->exec = PC_EXEC_STEPWISE;
   o->polish = 0;
-  o->mem_budget_bytes = int64_t(64) << 30;
-  o->request_max_bytes = int64_t(8) << 30;
+  o->mem_budget_bytes = int64_t(160) << 30;
+  o->request_max_bytes = int64_t(64) << 30;
 }
 
 pc_status pc_server_create(pc_server** out, int device, const pc_server_options* opt) {

@@ -57,6 +57,29 @@ def test_each_result_same_alone_and_in_the_mix(gpu):
             assert_same_complex(got, alone, coord_tol=1e-12, what=f"{net.widths}")
 
 
+def test_stream_requests_same_alone_and_in_the_mix(gpu):
+    """Requests of the configured serving stream itself (D up to 4, depth 2-6,
+    widths 16-128), the first 40 whose memory estimate is at most 2 GiB
+    (each takes at most ~20 ms): the same complex in an 8-slot mix as alone."""
+    reqs = [r for r in wl.serving_stream(300) if gpu.estimate_bytes(r.net) <= 2 << 30][:40]
+    assert max(r.net.D for r in reqs) == 4 and max(max(r.net.widths[1:]) for r in reqs) == 128
+    with gpu.Server(max_slots=8, precision="mixed", keep_outputs=True) as srv:
+        ids = [srv.submit(r.net, r.box) for r in reqs]
+        srv.wait_all(600)
+        mixed = []
+        for rid in ids:
+            st, res = srv.poll(rid)
+            assert st == 0 and res.status == 0, (res.status, srv.error(rid))
+            mixed.append(srv.outputs(rid))
+    with gpu.Extractor(precision="mixed", execution="stepwise", polish=0) as ex:
+        for r, (X, SIG, E) in zip(reqs, mixed):
+            ex.extract(r.net, r.box)
+            c = ex.counts()
+            alone = (ex.vertices(), unpack_codes(ex.sign_words(), c["P"]), ex.edges())
+            got = (X, unpack_codes(SIG, c["P"]), E)
+            assert_same_complex(got, alone, coord_tol=1e-12, what=f"stream request {r.rid} {r.net.widths}")
+
+
 def test_oversize_request_is_rejected(gpu):
     net, box = wl.random_mlp(4, 6, 128, seed=1)
     with gpu.Server(max_slots=2, request_max_bytes=1 << 30) as srv:
