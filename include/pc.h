@@ -136,6 +136,13 @@ typedef struct {
                              extraction returns PC_ERR_TIMEOUT; exercises the
                              bounded-wait error path without hanging the GPU.
                              No effect in PC_EXEC_STEPWISE (no grid barrier) */
+  double filter_kappa_audit; /* PC_PREC_MIXED, 0 = off: values with
+                             filter_kappa < |z| / estimate <= this are also
+                             evaluated in FP64 at the exact vertex, but only
+                             recorded (pc_diagnostics: signs the filter would
+                             have missed, and their largest margin), never
+                             written back, so the extraction is the one that
+                             filter_kappa alone gives */
 } pc_options;
 
 /* Fills *opt with defaults (mixed precision, persistent execution,
@@ -281,7 +288,10 @@ pc_status pc_poset_level(pc_ctx *ctx, int k, int64_t *n_cells, int64_t *n_parent
  * FP64 re-decisions that changed the FP32 sign (PC_PREC_MIXED), and the
  * largest |z| / (FP32 error estimate of z) among those, times 1000 and
  * rounded up (the filter re-decides every |z| <= filter_kappa x estimate, so
- * a margin near filter_kappa means a flip close to the filter's edge). */
+ * a margin near filter_kappa means a flip close to the filter's edge); then,
+ * with filter_kappa_audit, the FP32 signs beyond filter_kappa that FP64 shows
+ * wrong (each one an error the filter let through) and their largest
+ * margin, times 1000. */
 pc_status pc_diagnostics(pc_ctx *ctx, int64_t *out, int n);
 
 /* With opt.timers: device time in ms of the last extraction's kernels,

@@ -59,7 +59,8 @@ class Options(ctypes.Structure):
                 ("mem_budget_bytes", ctypes.c_int64), ("filter_kappa", ctypes.c_double),
                 ("polish", ctypes.c_int), ("polish_tol", ctypes.c_double), ("timers", ctypes.c_int),
                 ("gemm", ctypes.c_int), ("pairing", ctypes.c_int), ("canonical", ctypes.c_int),
-                ("prune", ctypes.c_int), ("debug_barrier_timeout", ctypes.c_int)]
+                ("prune", ctypes.c_int), ("debug_barrier_timeout", ctypes.c_int),
+                ("filter_kappa_audit", ctypes.c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -176,6 +177,9 @@ class Extractor:
     10 (libpc_d10.so, the same kernels with larger per-vertex arrays).
     debug_barrier_timeout: testing only; the persistent kernel's grid barriers
     time out on purpose (bounded), so extract() raises PC_ERR_TIMEOUT.
+    kappa_audit: mixed precision; also checks (in FP64, without changing the
+    result) the signs between kappa and kappa_audit error estimates, and
+    counts those the filter let through wrong (diagnostics "missed").
     """
 
     def __init__(self, device: int = 0, precision: str = "mixed", execution: str = "persistent",
@@ -183,7 +187,7 @@ class Extractor:
                  mem_budget_bytes: int = 0, kappa: float = 12.0, polish: int = -1, polish_tol: float = 1e-6,
                  timers: bool = False, torch_allocator: bool = True, gemm: str = "tensor",
                  pairing: str = "deferred", canonical: bool = False, prune: bool = False, max_dim: int = 8,
-                 debug_barrier_timeout: bool = False):
+                 debug_barrier_timeout: bool = False, kappa_audit: float = 0.0):
         if not 1 <= max_dim <= 10:
             raise ValueError("max_dim must be in [1, 10]")
         self._lib = load_library(LIB if max_dim <= 8 else LIB_D10)
@@ -204,6 +208,7 @@ class Extractor:
         o.canonical = int(canonical)
         o.prune = int(prune)
         o.debug_barrier_timeout = int(debug_barrier_timeout)
+        o.filter_kappa_audit = float(kappa_audit)
         self.device = device
         self.options = o
         self._ctx = ctypes.c_void_p()
@@ -318,10 +323,10 @@ class Extractor:
         return out
 
     def diagnostics(self) -> dict:
-        out = np.zeros(13, np.int64)
-        self._check(self._lib.pc_diagnostics(self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 13))
+        out = np.zeros(15, np.int64)
+        self._check(self._lib.pc_diagnostics(self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 15))
         keys = ["launches", "grows", "polished", "degenerate", "undecided", "vcap", "ecap", "tcap",
-                "bytes", "persistent_ctas", "reruns", "flips", "flip_margin_milli"]
+                "bytes", "persistent_ctas", "reruns", "flips", "flip_margin_milli", "missed", "missed_margin_milli"]
         return dict(zip(keys, (int(x) for x in out)))
 
     def kernel_times_ms(self) -> np.ndarray:

@@ -283,6 +283,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_step(NetDesc net, State st, int l
   extern __shared__ double dsm[];
   __shared__ Smem sm;
   if (cta_stopped(st)) return;
+  if (threadIdx.x == 0) sm.nrl_layer = -1;
+  __syncthreads();
   phase_step<ZT, MIXED>(net, st, l, i, sm, dsm, mw);
 }
 
@@ -304,6 +306,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_layer(NetDesc net, State st, int 
   if (cta_stopped(st)) return;
   unsigned int passed = 0;
   const int H = net.w[l + 1];
+  if (threadIdx.x == 0) sm.nrl_layer = -1;
+  __syncthreads();
   if (prologue) {
     phase_decide<ZT, MIXED>(net, st, l, sm, dsm, mw);
     if (!grid_barrier(st.g, passed)) return;  // uniform per CTA
@@ -812,6 +816,7 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   net.precision = c->opt.precision;
   net.kappa = static_cast<float>(c->opt.filter_kappa > 0 ? c->opt.filter_kappa : 2.0);
   net.debug_barrier = c->opt.debug_barrier_timeout ? 1 : 0;
+  net.kappa_sel = std::max(net.kappa, static_cast<float>(c->opt.filter_kappa_audit));
   long long p = 0;
   int n = 0, hmax = 0, mw = D;
   for (int l = 0; l <= L; ++l) {
@@ -968,6 +973,8 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     g0.error = g.error;
     g0.flips = g.flips;
     g0.flip_margin_bits = g.flip_margin_bits;
+    g0.missed = g.missed;
+    g0.missed_margin_bits = g.missed_margin_bits;
     g0.barrier_extra = net.debug_barrier ? 1u : 0u;
     *static_cast<Global*>(c->h_g) = g0;
     PC_CUDA(cudaMemcpyAsync(c->g, c->h_g, sizeof(Global), cudaMemcpyHostToDevice, c->stream));
@@ -1003,11 +1010,15 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   PC_CUDA(cudaStreamSynchronize(c->stream));
   c->polished = static_cast<Global*>(c->h_g)->polished;
   c->flips = static_cast<Global*>(c->h_g)->flips;
+  c->missed = static_cast<Global*>(c->h_g)->missed;
   {
-    const int bits = static_cast<Global*>(c->h_g)->flip_margin_bits;
+    int bits = static_cast<Global*>(c->h_g)->flip_margin_bits;
     float f = 0.f;
     std::memcpy(&f, &bits, sizeof(f));
     c->flip_margin = f;
+    bits = static_cast<Global*>(c->h_g)->missed_margin_bits;
+    std::memcpy(&f, &bits, sizeof(f));
+    c->missed_margin = f;
   }
   for (int k = 0; k <= pc_ctx::kPolishSlot; ++k) {
     c->ktime_ms[k] = -1.0;
@@ -1342,10 +1353,11 @@ pc_status pc_stats(pc_ctx* c, int64_t* out, int n_neurons) {
 
 pc_status pc_diagnostics(pc_ctx* c, int64_t* out, int n) {
   if (!c || !out) return PC_ERR_INVALID;
-  const int64_t v[13] = {c->launches, c->grows, c->polished, c->degenerate, c->undecided, c->Vcap,
+  const int64_t v[15] = {c->launches, c->grows, c->polished, c->degenerate, c->undecided, c->Vcap,
                          c->Ecap,    c->Tcap,  (int64_t)c->allocated, c->grid_persist, c->reruns, c->flips,
-                         (int64_t)std::ceil(1000.0 * c->flip_margin)};
-  for (int k = 0; k < n && k < 13; ++k) out[k] = v[k];
+                         (int64_t)std::ceil(1000.0 * c->flip_margin), c->missed,
+                         (int64_t)std::ceil(1000.0 * c->missed_margin)};
+  for (int k = 0; k < n && k < 15; ++k) out[k] = v[k];
   return PC_OK;
 }
 
@@ -1470,6 +1482,7 @@ extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const doub
     net.m = 2 * D;
     net.precision = precision;
     net.kappa = static_cast<float>(c.opt.filter_kappa);
+    net.kappa_sel = net.kappa;
     long long q = 0;
     int nn = 0, hmax = 0, mw = D;
     for (int l = 0; l <= L; ++l) net.w[l] = widths[l];

@@ -110,6 +110,8 @@ struct pc_ctx {
   long long launches = 0;
   long long flips = 0;       // FP64 re-decisions that changed an FP32 sign
   float flip_margin = 0.f;   // largest |z| / estimate among them
+  long long missed = 0;      // audit band: wrong FP32 signs beyond kappa
+  float missed_margin = 0.f;
   bool have_result = false;
 
   // per-layer kernel timers (opt.timers)

@@ -78,6 +78,7 @@ struct NetDesc {
   const float* norms;    // per layer: [2l] = max_j ||W_j||_2, [2l+1] = max_j |b_j|
   const float* nrm;      // per neuron n: [3n] = ||W_n||_2, [3n+1] = |b_n|, [3n+2] = 1/||W_n||_2
   float kappa;           // filter factor
+  float kappa_sel;       // values with |z| <= kappa_sel x estimate go to FP64: max(kappa, audit band)
   // Polyhedral domain {x : c - A x >= 0} (Section 4.1): facet i of the m
   // entries has the value fc[i] - fA[i, :] x (fA row-major m x D, device).
   // Both null for the box [lo, hi], whose facet 2d is x_d - lo_d and 2d+1
@@ -103,6 +104,8 @@ struct Global {
   int error;             // sticky kErr* bits
   int flips;             // FP64 re-decisions that changed the FP32 sign
   int flip_margin_bits;  // largest |z| / (FP32 error estimate) among them (float bits)
+  int missed;            // audit band: wrong FP32 signs beyond kappa (not written back)
+  int missed_margin_bits;
   unsigned int barrier;  // grid barrier arrival counter (reset per launch)
   unsigned int barrier_extra;  // arrivals a barrier waits for beyond the grid: 0, or 1 to test the timeout path
   long long need_v, need_e, need_t;

@@ -39,7 +39,7 @@
 namespace pc {
 
 constexpr int kPairCap = 1024;         // intersecting edges a CTA buffers before it appends them
-constexpr int kLaCap = 512;            // look-ahead list entries a CTA buffers
+constexpr int kLaCap = 1024;           // look-ahead list entries a CTA buffers
 constexpr int kPendCap = 2 * kBlock;   // vertices a CTA queues for an FP64 re-decision
 
 struct Smem {
@@ -53,8 +53,11 @@ struct Smem {
   int cursor;
   int npend;
   int wcnt[kWarps];
+  int use_smem;
   long long pbase, lbase, sbase;
   int zlist[kWarps][16];
+  float nrl[3 * kMaxWidth];            // the layer's per-neuron norms (NetDesc::nrm)
+  int nrl_layer;                       // layer staged in nrl, -1: none
   int nzl[kMaxD + 2];
   NewtonOut nout;
   long long acc[4];
@@ -133,12 +136,19 @@ __device__ void redecide_cta(const NetDesc& net, const State& st, long long v, i
   for (int j = j_from + threadIdx.x; j < H; j += blockDim.x) {
     const float z32 = static_cast<float>(Z[(long long)j * Vcap + v]);
     const float est = net.nrm[3 * (n0 + j)] * esc + 2.9802322e-8f * net.nrm[3 * (n0 + j) + 1];
-    if (!(fabsf(z32) <= net.kappa * est)) continue;
+    if (!(fabsf(z32) <= net.kappa_sel * est)) continue;
     double zs = rows.val[j];
     if (sm.nout.ok)
       for (int d = 0; d < D; ++d) zs += static_cast<double>(rows.grad[j * D + d]) * sm.nout.dlt[d];
     const bool und = !sm.nout.ok || fabs(zs) <= 1e-12 * rows.scale[j];
     const bool minus = zs < 0.0;
+    if (!(fabsf(z32) <= net.kappa * est)) {  // audit band: record a wrong FP32 sign, change nothing
+      if ((z32 < 0.f) != minus && !und) {
+        atomicAdd(&st.g->missed, 1);
+        atomicMax(&st.g->missed_margin_bits, __float_as_int(fabsf(z32) / est));
+      }
+      continue;
+    }
     ZT zz = static_cast<ZT>(zs);
     if (!minus && !(zz > ZT(0))) zz = tiny_value<ZT>();
     if (minus && !(zz < ZT(0))) zz = -tiny_value<ZT>();
@@ -194,7 +204,7 @@ __device__ __noinline__ void phase_decide(const NetDesc& net, const State& st, i
         }
         if (MIXED)
           filt = filt || fabsf(static_cast<float>(z)) <=
-                             net.kappa * (net.nrm[3 * (n0 + j)] * esc + 2.9802322e-8f * net.nrm[3 * (n0 + j) + 1]);
+                             net.kappa_sel * (net.nrm[3 * (n0 + j)] * esc + 2.9802322e-8f * net.nrm[3 * (n0 + j) + 1]);
       }
       if (filt) sm.pend[atomicAdd(&sm.npend, 1)] = v;
     }
@@ -223,6 +233,8 @@ struct ScanTile {
   int nvalid;
 };
 
+// nE may be the edge capacity (a load issued before the count is known):
+// scan_edges takes the valid edges from the actual count.
 __device__ __forceinline__ ScanTile scan_load(const State& st, const uint32_t* fcur, long long idx0, long long nE,
                                               bool classify) {
   ScanTile T;
@@ -247,19 +259,29 @@ __device__ __forceinline__ ScanTile scan_load(const State& st, const uint32_t* f
   return T;
 }
 
+__device__ __forceinline__ long long scan_first_idx0() {
+  return (long long)blockIdx.x * (4ll * kBlock) + (threadIdx.x >> 5) * 128 + 4 * (threadIdx.x & 31);
+}
+
+// first: this lane's part of the CTA's first iteration (scan_load at
+// scan_first_idx0()), loaded by the caller early.  The entries go to the
+// CTA's look-ahead buffer sm.la while it has room (the caller flushes it),
+// else straight to the list with one reservation per CTA iteration.
 template <typename ZT>
 __device__ void scan_edges(const State& st, const ZT* zrow, long long nE, long long nV, uint32_t* fcur,
-                           bool classify, int4* lnext, uint32_t* fnext, long long* counter, int n, Smem& sm) {
+                           bool classify, int4* lnext, uint32_t* fnext, long long* counter, int n, Smem& sm,
+                           const ScanTile& first) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long G = gridDim.x;
   constexpr long long kSpan = 4ll * kBlock;
   const long long iters = (nE + kSpan * G - 1) / (kSpan * G);
   // the next iteration's flags and endpoints are loaded while this one is classified
-  ScanTile nxt = scan_load(st, fcur, blockIdx.x * kSpan + warp * 128 + 4 * lane, nE, classify);
+  ScanTile nxt = first;
   for (long long it = 0; it < iters; ++it) {
     const long long idx0 = (it * G + blockIdx.x) * kSpan + warp * 128 + 4 * lane;
     const ScanTile T = nxt;
     if (it + 1 < iters) nxt = scan_load(st, fcur, idx0 + kSpan * G, nE, classify);
+    const int nvalid = idx0 >= nE ? 0 : (nE - idx0 >= 4 ? 4 : int(nE - idx0));
     const uint32_t skip = (T.fw >> (idx0 & 31)) & 0xFu;
     if (fcur != nullptr) {
       __syncwarp();
@@ -273,7 +295,7 @@ __device__ void scan_edges(const State& st, const ZT* zrow, long long nE, long l
     uint32_t nib = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      if (q >= T.nvalid || ((skip >> q) & 1u)) continue;
+      if (q >= nvalid || ((skip >> q) & 1u)) continue;
       const int u = pu[q], w = pw[q];
       if (u < 0 || u >= nV || w < 0 || w >= nV) {
         report_corrupt(st.g, 6, n, idx0 + q, u, w);  // never index with it
@@ -299,20 +321,37 @@ __device__ void scan_edges(const State& st, const ZT* zrow, long long nE, long l
         sm.wcnt[w] = int(tot);
         tot += cw;
       }
-      sm.sbase = tot ? atomic_add_ll(counter, tot) : 0;
+      if (sm.nla + tot <= kLaCap) {
+        sm.use_smem = 1;
+        sm.sbase = sm.nla;
+        sm.nla += int(tot);
+      } else {
+        sm.use_smem = 0;
+        sm.sbase = atomic_add_ll(counter, tot);
+      }
     }
     __syncthreads();
     if (c) {
       const long long base = sm.sbase + sm.wcnt[warp] + (x - c);
-      for (int t = 0; t < c; ++t) lnext[base + t] = ent[t];
+      if (sm.use_smem) {
+        for (int t = 0; t < c; ++t) sm.la[base + t] = ent[t];  // flagged when flushed
+      } else {
+        for (int t = 0; t < c; ++t) lnext[base + t] = ent[t];
+      }
     }
-    uint32_t word = nib << (idx0 & 31);  // the 8 lanes of a flag word OR their nibbles
-    word |= __shfl_xor_sync(0xffffffffu, word, 1);
-    word |= __shfl_xor_sync(0xffffffffu, word, 2);
-    word |= __shfl_xor_sync(0xffffffffu, word, 4);
-    if ((lane & 7) == 0 && word) atomicOr(fnext + (idx0 >> 5), word);
+    if (!sm.use_smem) {
+      uint32_t word = nib << (idx0 & 31);  // the 8 lanes of a flag word OR their nibbles
+      word |= __shfl_xor_sync(0xffffffffu, word, 1);
+      word |= __shfl_xor_sync(0xffffffffu, word, 2);
+      word |= __shfl_xor_sync(0xffffffffu, word, 4);
+      if ((lane & 7) == 0 && word) atomicOr(fnext + (idx0 >> 5), word);
+    }
+    __syncthreads();  // sm.use_smem / sbase are reused by the next iteration
   }
 }
+
+__device__ void flush_cta(const State& st, Counters* cur, long long* cnext, int4* lnext, uint32_t* fnext,
+                          long long ebase, bool ahead, Smem& sm);
 
 // Layer start, step (3) for neuron 0 of layer l.
 template <typename ZT>
@@ -324,7 +363,17 @@ __device__ void phase_scan0(const NetDesc& net, const State& st, int l, Smem& sm
     return;
   }
   const ZT* zrow = static_cast<const ZT*>(st.Z[l]);
-  scan_edges<ZT>(st, zrow, nE, nV, nullptr, true, st.list[n0 & 1], st.flags[n0 & 1], &st.cnt[n0 + 1].nsplit, n0, sm);
+  if (threadIdx.x == 0) {
+    sm.npairs = 0;
+    sm.npairla = 0;
+    sm.nla = 0;
+  }
+  __syncthreads();
+  const ScanTile first = scan_load(st, nullptr, scan_first_idx0(), nE, true);
+  scan_edges<ZT>(st, zrow, nE, nV, nullptr, true, st.list[n0 & 1], st.flags[n0 & 1], &st.cnt[n0 + 1].nsplit, n0, sm,
+                 first);
+  __syncthreads();
+  if (sm.nla) flush_cta(st, nullptr, &st.cnt[n0 + 1].nsplit, st.list[n0 & 1], st.flags[n0 & 1], 0, true, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -472,6 +521,9 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
     sm.npend = 0;
     sm.acc[0] = sm.acc[1] = 0;
   }
+  if (sm.nrl_layer != l) {  // uniform: set by the previous step of this launch, or -1
+    for (int t = threadIdx.x; t < 3 * H; t += kBlock) sm.nrl[t] = net.nrm[3 * net.off[l] + t];
+  }
   // the table of the previous step: emptied for the step after this one
   {
     uint64_t* told = st.table + (long long)((n + 1) & 1) * 2 * st.Tcap;
@@ -479,6 +531,7 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
     for (long long t = (long long)blockIdx.x * kBlock + threadIdx.x; t < tprev; t += G * kBlock) told[t] = kEmpty;
   }
   __syncthreads();
+  if (threadIdx.x == 0) sm.nrl_layer = l;
   const long long Vcap = st.Vcap;
   ZT* Z = static_cast<ZT*>(st.Z[l]);
   const int e = m + n;
@@ -488,7 +541,7 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
   long long* cnext = ahead ? &st.cnt[n + 2].nsplit : nullptr;
   uint64_t* table = st.table + (long long)(n & 1) * 2 * st.Tcap;
   const long long tmask = tneed - 1;
-  const float* nrl = net.nrm + 3 * net.off[l];
+  const float* nrl = sm.nrl;
   int* zlist = sm.zlist[warp];
   long long nkeys_w = 0, ndeg_w = 0;
   int err_w = 0;
@@ -543,12 +596,19 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
       }
       const double a = static_cast<double>(za0);
       const double b = static_cast<double>(zb0);
-      double t = a / (a - b);
-      bad = !(a > 0.0 && b < 0.0);
-      if (!(t >= 0.0 && t <= 1.0)) {
-        t = t < 0.0 ? 0.0 : 1.0;
-        bad = true;
+      // t in float64 on one lane (the FP64 units are few), then broadcast
+      double t = 0.0;
+      int out_of_range = 0;
+      if (lane == 0) {
+        t = a / (a - b);
+        if (!(t >= 0.0 && t <= 1.0)) {
+          t = t < 0.0 ? 0.0 : 1.0;
+          out_of_range = 1;
+        }
       }
+      t = __shfl_sync(0xffffffffu, t, 0);
+      out_of_range = __shfl_sync(0xffffffffu, out_of_range, 0);
+      bad = !(a > 0.0 && b < 0.0) || out_of_range;
       if (lane < D) st.X[(long long)lane * Vcap + v0] = fma(t, xq - xp, xp);
       const ZT tz = static_cast<ZT>(t);
       // earlier layers' entries: the join of the endpoints' words
@@ -634,7 +694,7 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
           for (int j = lane; j < H; j += 32) {
             if (j <= i) continue;
             const float zv = j < 64 ? zk[j >> 5] : static_cast<float>(Z[(long long)j * Vcap + v0]);
-            f = f || fabsf(zv) <= net.kappa * (nrl[3 * j] * esc0 + 2.9802322e-8f * nrl[3 * j + 1]);
+            f = f || fabsf(zv) <= net.kappa_sel * (nrl[3 * j] * esc0 + 2.9802322e-8f * nrl[3 * j + 1]);
           }
           pend = __any_sync(0xffffffffu, f);
         }
@@ -832,10 +892,12 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
     if (sm.acc[0]) atomic_add_ll(&cur->nkeys, sm.acc[0]);
     if (sm.acc[1]) atomic_add_ll(&cur->ndegenerate, sm.acc[1]);
   }
-  if (sm.npairs || sm.nla) flush_cta(st, cur, cnext, lnext, fnext, nE + total, ahead, sm);
   // step (3) for the next neuron over the edges that did not split here
   const ZT* znext = Z + (long long)(ahead ? i + 1 : 0) * Vcap;
-  scan_edges<ZT>(st, znext, nE, nV, st.flags[n & 1], ahead, lnext, fnext, cnext, n, sm);
+  const ScanTile scan_first = scan_load(st, st.flags[n & 1], scan_first_idx0(), nE, ahead);
+  scan_edges<ZT>(st, znext, nE, nV, st.flags[n & 1], ahead, lnext, fnext, cnext, n, sm, scan_first);
+  __syncthreads();
+  if (sm.npairs || sm.nla) flush_cta(st, cur, cnext, lnext, fnext, nE + total, ahead, sm);
   return false;
 }
 

@@ -15,7 +15,7 @@ int main(void) {
   F(pc_options, init_vcap); F(pc_options, init_ecap); F(pc_options, mem_budget_bytes);
   F(pc_options, filter_kappa); F(pc_options, polish); F(pc_options, polish_tol); F(pc_options, timers);
   F(pc_options, gemm); F(pc_options, pairing); F(pc_options, canonical); F(pc_options, prune);
-  F(pc_options, debug_barrier_timeout);
+  F(pc_options, debug_barrier_timeout); F(pc_options, filter_kappa_audit);
   Z(pc_options);
   F(pc_server_options, max_slots); F(pc_server_options, precision); F(pc_server_options, exec);
   F(pc_server_options, polish); F(pc_server_options, keep_outputs); F(pc_server_options, mem_budget_bytes);
