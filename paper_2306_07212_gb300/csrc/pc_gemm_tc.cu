@@ -346,6 +346,198 @@ __global__ void __launch_bounds__(kTcTileM, 1) k_gemm_tc(NetDesc net, State st, 
   }
 }
 
+
+// The same product, scheduled for overlap and occupancy (layers whose
+// operands fit: all pieces of one 32-input chunk get their own buffer).
+// Per chunk: the pieces are written, one barrier, one thread issues the
+// chunk's MMAs (one accumulator per 8-input K step, tail products first),
+// the next chunk is gathered while they run, and the chunk's four
+// accumulators are read back into a running FP32 sum in K-step order -- the
+// sum the epilogue of k_gemm_tc forms, so the results agree bit for bit
+// where k_gemm_tc gives every K step its own accumulator.  Tensor memory
+// holds one chunk's accumulators (4 x 64 columns for layers up to 64 wide),
+// so two CTAs share an SM.
+__device__ __forceinline__ void gather_chunk(const State& st, const float* Zin, long long Vcap, long long v,
+                                             bool valid, int q, int K, int ebase, float (&x)[kTcChunkK]) {
+  uint64_t word = 0;
+  int cw = -1;
+#pragma unroll
+  for (int k0 = 0; k0 < kTcChunkK; ++k0) {
+    const int k = q * kTcChunkK + k0;
+    float a = 0.f;
+    if (valid && k < K) {
+      const int entry = ebase + k, wi = entry >> 5;
+      if (wi != cw) {
+        word = st.SIG[(long long)wi * Vcap + v];
+        cw = wi;
+      }
+      if (((word >> (2 * (entry & 31))) & 3ull) == kPlus) a = Zin[(long long)k * Vcap + v];
+    }
+    x[k0] = a;
+  }
+}
+
+template <int PIECES>
+__global__ void __launch_bounds__(kTcTileM, 2) k_gemm_tc2(NetDesc net, State st, int l, int Npad, int Kpad) {
+  extern __shared__ unsigned char tc_raw[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ float bias[kTcMaxN];
+  __shared__ int fail;
+  if (cta_stopped(st)) return;
+  const Counters* c = st.cnt + net.off[l];
+  const long long nV = c->nV_before + c->nsplit;
+  if (nV < 0 || nV > st.Vcap) {  // uniform: every thread reads the same counters
+    if (threadIdx.x == 0) report_corrupt(st.g, 1, l, nV, st.Vcap, 0);
+    return;
+  }
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int H = net.w[l + 1], K = net.w[l], KC = Kpad / kTcChunkK;
+  const uint32_t chunkB = static_cast<uint32_t>(Npad) * 128u;
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+  unsigned char* Bp = base;                         // [piece][chunk][Npad rows][128 B]
+  unsigned char* Abuf = Bp + PIECES * KC * chunkB;  // one buffer per piece of a chunk
+  const double* W = net.W64 + net.wofs[l];
+  for (int idx = tid; idx < Npad * Kpad; idx += blockDim.x) {
+    const int j = idx / Kpad, k = idx % Kpad;
+    double r = (j < H && k < K) ? W[(long long)j * K + k] : 0.0;
+    const uint32_t off = (k / kTcChunkK) * chunkB + sw128_offset(j, k % kTcChunkK);
+#pragma unroll
+    for (int pc = 0; pc < PIECES; ++pc) {
+      const uint32_t w = to_tf32(static_cast<float>(r));
+      *reinterpret_cast<uint32_t*>(Bp + pc * KC * chunkB + off) = w;
+      r -= static_cast<double>(__uint_as_float(w));
+    }
+  }
+  for (int j = tid; j < kTcMaxN; j += blockDim.x)
+    bias[j] = j < H ? static_cast<float>(net.W64[net.bofs[l] + j]) : 0.f;
+  if (tid == 0) {
+    fail = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+  }
+  int stride = 32;  // columns per accumulator (a power of two >= Npad)
+  while (stride < Npad) stride <<= 1;
+  constexpr int kSteps = kTcChunkK / 8;  // K steps (accumulators) per chunk
+  const int ncols = kSteps * stride;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = tf32_idesc(kTcTileM, Npad);
+  const long long Vcap = st.Vcap;
+  const float* Zin = static_cast<const float*>(st.Z[l - 1]);
+  float* Zout = static_cast<float*>(st.Z[l]);
+  const int ebase = net.m + net.off[l - 1];
+  const int ng = Npad / 16;  // 16-column groups of the output
+  uint32_t parity = 0u;
+  float x[kTcChunkK];  // the chunk being split; the next one is gathered during the MMAs
+
+  for (long long tile = blockIdx.x; tile * kTcTileM < nV; tile += gridDim.x) {
+    const long long v = tile * kTcTileM + tid;
+    const bool valid = v < nV;
+    float acc[kTcMaxN];  // running sum of the K steps' accumulators (row tid)
+#pragma unroll
+    for (int j = 0; j < kTcMaxN; ++j) acc[j] = 0.f;
+    float a2 = 0.f;
+    gather_chunk(st, Zin, Vcap, v, valid, 0, K, ebase, x);
+    for (int q = 0; q < KC; ++q) {
+      // the pieces of this chunk (the previous chunk's MMAs have completed)
+#pragma unroll
+      for (int k0 = 0; k0 < kTcChunkK; ++k0) a2 = fmaf(x[k0], x[k0], a2);
+#pragma unroll
+      for (int pa = 0; pa < PIECES; ++pa) {
+        unsigned char* A = Abuf + pa * kTcAChunkBytes;
+#pragma unroll
+        for (int g = 0; g < kTcChunkK / 4; ++g) {
+          uint32_t u[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {  // piece pa of x: split again from the value
+            float r = x[g * 4 + e];
+            uint32_t pc = to_tf32(r);
+#pragma unroll
+            for (int kk = 0; kk < PIECES - 1; ++kk)
+              if (kk < pa) {
+                r -= __uint_as_float(pc);
+                pc = to_tf32(r);
+              }
+            u[e] = pc;
+          }
+          *reinterpret_cast<uint4*>(A + sw128_offset(tid, g * 4)) = make_uint4(u[0], u[1], u[2], u[3]);
+        }
+      }
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0 && !fail) {
+#pragma unroll
+        for (int kk = 0; kk < kSteps; ++kk) {  // 8 TF32 (32 B) per MMA
+          const uint32_t o = kk * 32;
+          const uint32_t dacc = tmem + static_cast<uint32_t>(kk * stride);
+          bool fresh = true;  // the first product into an accumulator overwrites it
+          for (int pa = PIECES - 1; pa >= 0; --pa)      // tail pieces of the values first,
+            for (int pw = PIECES - 1 - pa; pw >= 0; --pw) {  // then smaller products first
+              const uint32_t aa = smem_u32(Abuf + pa * kTcAChunkBytes);
+              const uint32_t bb = smem_u32(Bp + (pw * KC + q) * chunkB);
+              mma_tf32(dacc, sw128_desc(aa + o), sw128_desc(bb + o), idesc, fresh ? 0 : 1);
+              fresh = false;
+            }
+        }
+        mma_commit(&bar);
+      }
+      if (q + 1 < KC) gather_chunk(st, Zin, Vcap, v, valid, q + 1, K, ebase, x);  // while the MMAs run
+      if (!mbar_wait(&bar, parity)) fail = 1;
+      parity ^= 1u;
+      tc_fence_after();
+      // this chunk's K steps, in order, into the running sum
+#pragma unroll
+      for (int kk = 0; kk < kSteps; ++kk) {
+#pragma unroll
+        for (int g = 0; g < kTcMaxN / 16; ++g) {
+          if (g >= ng) break;
+          float r[16];
+          tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(kk * stride + g * 16), r);
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) acc[g * 16 + jj] += r[jj];
+        }
+      }
+      tc_fence_before();
+      if (__syncthreads_or(fail)) break;
+    }
+    if (fail) break;
+    if (valid) {
+#pragma unroll
+      for (int g = 0; g < kTcMaxN / 16; ++g) {
+        if (g >= ng) break;
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj)
+          if (g * 16 + jj < H) Zout[(long long)(g * 16 + jj) * Vcap + v] = acc[g * 16 + jj] + bias[g * 16 + jj];
+      }
+      // error scale (as in k_gemm_tc with one accumulator per K step)
+      const float u = 5.9604645e-8f;  // 2^-24
+      float rho = (PIECES == 2 ? 8.f * u : 0.5f * u) * sqrtf(a2);
+      const float inh = net.norms[2 * (l - 1)] * st.esc[v] + 0.5f * u * net.norms[2 * (l - 1) + 1];
+      rho = sqrtf(rho * rho + inh * inh);
+      st.esc[v] = rho;
+    }
+  }
+  if (fail && tid == 0) atomicOr(&st.g->error, kErrTimeout);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
 }  // namespace pc
 
 using namespace pc;
@@ -356,10 +548,21 @@ bool pc_gemm_tc_eligible(const NetDesc& net, int l) {
   return l >= 1 && net.w[l + 1] <= kTcMaxN && net.w[l] <= kTcMaxK;
 }
 
+// Shared memory of k_gemm_tc2: W^T pieces for all of K, one buffer per piece
+// of a chunk, alignment and slack.
+__host__ __device__ constexpr int tc2_smem_bytes(int pieces, int kc, int npad) {
+  return pieces * kc * npad * 128 + pieces * kTcAChunkBytes + 2048;
+}
+constexpr int kTc2SmemMax = 220 * 1024;  // dynamic; the static shared memory comes on top
+
 cudaError_t pc_gemm_tc_set_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax);
   const cudaError_t e2 = cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax);
-  return e != cudaSuccess ? e : e2;
+  const cudaError_t e3 = cudaFuncSetAttribute(k_gemm_tc2<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTc2SmemMax);
+  const cudaError_t e4 = cudaFuncSetAttribute(k_gemm_tc2<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTc2SmemMax);
+  if (e != cudaSuccess) return e;
+  if (e2 != cudaSuccess) return e2;
+  return e3 != cudaSuccess ? e3 : e4;
 }
 
 cudaError_t pc_gemm_tc_launch(const NetDesc& net, const State& st, int l, long long vcap_tiles, int num_sms,
@@ -367,6 +570,18 @@ cudaError_t pc_gemm_tc_launch(const NetDesc& net, const State& st, int l, long l
   const int H = net.w[l + 1], K = net.w[l];
   const int Npad = (H + 15) / 16 * 16;
   const int Kpad = (K + kTcChunkK - 1) / kTcChunkK * kTcChunkK;
+  const size_t smem2 = static_cast<size_t>(tc2_smem_bytes(pieces, Kpad / kTcChunkK, Npad));
+  if (smem2 <= static_cast<size_t>(kTc2SmemMax)) {
+    int stride = 32;
+    while (stride < Npad) stride <<= 1;
+    const int tmem_per_sm = 512 / (4 * stride);
+    const int per_sm = std::max(1, std::min({2, tmem_per_sm, static_cast<int>(228 * 1024 / (smem2 + 1024))}));
+    const int grid =
+        static_cast<int>(std::max<long long>(1, std::min<long long>((long long)num_sms * per_sm, vcap_tiles)));
+    if (pieces == 3) k_gemm_tc2<3><<<grid, kTcTileM, smem2, stream>>>(net, st, l, Npad, Kpad);
+    else k_gemm_tc2<2><<<grid, kTcTileM, smem2, stream>>>(net, st, l, Npad, Kpad);
+    return cudaGetLastError();
+  }
   const size_t smem = static_cast<size_t>(tc_smem_bytes(pieces, Kpad / kTcChunkK, Npad));
   // CTAs per SM that shared and tensor memory allow (the kernel allocates
   // accumulators up to 512 columns; a CTA waits in tcgen05.alloc while
