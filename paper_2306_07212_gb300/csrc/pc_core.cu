@@ -998,7 +998,9 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
     const size_t stage_b = (n_stage * 8 + 15) / 16 * 16;
     const int wpc = std::max(1, std::min(kWarps, int((kPolishSmemMax - stage_b) / ws)));
     TimerScope ts(c, pc_ctx::kPolishSlot);
-    if (dom)
+    if (pc_polish_tile_eligible(net))
+      PC_CUDA(pc_polish_tile_launch(net, make_state(c), thr, c->mw, c->num_sms, dom, c->stream));
+    else if (dom)
       k_polish<true><<<c->grid_step, 32 * wpc, stage_b + ws * wpc, c->stream>>>(net, make_state(c), thr, c->mw, n_stage);
     else
       k_polish<false><<<c->grid_step, 32 * wpc, stage_b + ws * wpc, c->stream>>>(net, make_state(c), thr, c->mw, n_stage);
@@ -1114,6 +1116,10 @@ static cudaError_t set_func_attributes_now() {
   set((const void*)k_polish<true>, kPolishSmemMax);
   {
     const cudaError_t r = pc_gemm_tc_set_attributes();
+    if (e == cudaSuccess) e = r;
+  }
+  {
+    const cudaError_t r = pc_polish_tile_set_attributes();
     if (e == cudaSuccess) e = r;
   }
   pc_adjoint_set_attributes();
@@ -1551,7 +1557,10 @@ extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const doub
       const long long n_stage = polish_stage(p, ws);
       const size_t stage_b = (n_stage * 8 + 15) / 16 * 16;
       const int wpc = std::max(1, std::min(kWarps, int((kPolishSmemMax - stage_b) / ws)));
-      k_polish<false><<<c.grid_step, 32 * wpc, stage_b + ws * wpc, c.stream>>>(net, make_state(&c), thr, c.mw, n_stage);
+      if (pc_polish_tile_eligible(net))
+        PC_CUDA(pc_polish_tile_launch(net, make_state(&c), thr, c.mw, c.num_sms, false, c.stream));
+      else
+        k_polish<false><<<c.grid_step, 32 * wpc, stage_b + ws * wpc, c.stream>>>(net, make_state(&c), thr, c.mw, n_stage);
       PC_CUDA(cudaGetLastError());
     }
     Global g{};

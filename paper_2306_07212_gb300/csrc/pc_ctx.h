@@ -34,6 +34,12 @@ cudaError_t pc_gemm_tc_set_attributes();
 cudaError_t pc_gemm_tc_launch(const pc::NetDesc& net, const pc::State& st, int l, long long vcap_tiles, int num_sms,
                               int pieces, cudaStream_t stream);
 
+// coordinate polish as a tiled product (pc_polish.cu), D <= 5
+bool pc_polish_tile_eligible(const pc::NetDesc& net);
+cudaError_t pc_polish_tile_set_attributes();
+cudaError_t pc_polish_tile_launch(const pc::NetDesc& net, const pc::State& st, float thr, int mw, int num_sms,
+                                  bool domain, cudaStream_t stream);
+
 struct PcError : std::runtime_error {
   pc_status status;
   PcError(pc_status s, const std::string& m) : std::runtime_error(m), status(s) {}
