@@ -12,9 +12,9 @@
 // so it runs as one: a CTA owns a tile of TV consecutive vertices (vertices
 // are created layer by layer, so a tile's vertices mostly need the same
 // layers), keeps the tile's activations (hi, lo) and gradients (D per input)
-// neuron-major in shared memory, and each thread accumulates a 4 x 4 block of
-// (vertex, neuron) outputs, so every activation and weight it loads serves
-// four outputs.  The dot products follow Ogita-Rump-Oishi Dot2 (exact
+// neuron-major in shared memory, and each thread accumulates a block of 4
+// vertices x kPtRows neurons, so every activation it loads serves kPtRows
+// outputs and every weight four.  The dot products follow Ogita-Rump-Oishi Dot2 (exact
 // products by FMA, TwoSum of the running sum, error terms summed in a
 // float), like newton_ff_warp; the layer's outputs overwrite its inputs
 // after a barrier.  D <= kPtMaxD; larger D takes the one-warp-per-vertex
@@ -31,6 +31,8 @@
 namespace pc {
 
 constexpr int kPtThreads = 256;
+constexpr int kPtRows = 2;       // neurons per thread (a thread's block: 4 vertices x kPtRows neurons)
+constexpr int kPtMinBlocks = 2;  // CTAs per SM the register allocation is made for
 constexpr int kPtMaxD = 5;
 constexpr int kPtSmemMax = 200 * 1024;
 
@@ -63,17 +65,19 @@ __host__ __device__ inline PtLayout pt_layout(int TV, int mw, int S, int D) {
   return p;
 }
 
-// Vertices per tile: the (vertex, neuron) 4 x 4 blocks of the widest layer
-// fill the CTA, at most 128 vertices, and the tile fits the shared memory.
+// Vertices per tile: the (vertex, neuron) blocks of the widest layer fill
+// the CTA, at most 128 vertices, and the tile fits the shared memory.
 static int pt_tile_vertices(int mw, int S, int D) {
-  const int nrg = (mw + 3) / 4;
+  const int nrg = (mw + kPtRows - 1) / kPtRows;
   int TV = std::min(128, 4 * std::max(1, kPtThreads / nrg));
   while (TV > 4 && pt_layout(TV, mw, S, D).total > (size_t)kPtSmemMax) TV -= 4;
   return TV;
 }
 
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
 template <int DT, bool DOMAIN>
-__global__ void __launch_bounds__(kPtThreads) k_polish_tile(NetDesc net, State st, float thr, int mw, int TV) {
+__global__ void __launch_bounds__(kPtThreads, kPtMinBlocks) k_polish_tile(NetDesc net, State st, float thr, int mw, int TV) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int s_lmax;
   __shared__ unsigned long long s_pol;
@@ -144,87 +148,103 @@ __global__ void __launch_bounds__(kPtThreads) k_polish_tile(NetDesc net, State s
     int in = DT;
     for (int k = 0; k <= lmax; ++k) {
       const int H = net.w[k + 1];
-      const int nrg = (H + 3) >> 2;
+      const int nrg = (H + kPtRows - 1) / kPtRows;
       const int p = threadIdx.x;
       const bool busy = p < nvg * nrg;
       const int vb = busy ? (p % nvg) * 4 : 0;  // vertex blocks vary fastest in a warp
-      const int rb = busy ? (p / nvg) * 4 : 0;
-      float s[4][4], e[4][4], jd[4][4][DT];
+      const int rb = busy ? (p / nvg) * kPtRows : 0;
+      // accumulators of vertex pairs (vb, vb + 1) and (vb + 2, vb + 3): the
+      // float-float arithmetic runs on packed FP32 pairs (two lanes of work
+      // per instruction, each rounded as the scalar operation)
+      float2 s2[2][kPtRows], e2[2][kPtRows], jd2[2][kPtRows][DT];
       if (busy) {
         const float2* Wt = net.WT2 + net.wofs[k];  // [in][H] (head, remainder)
         const float2* bk = net.WT2 + net.bofs[k];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < kPtRows; ++j) {
           const float2 b = rb + j < H ? bk[rb + j] : make_float2(0.f, 0.f);
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            s[i][j] = b.x;
-            e[i][j] = b.y;
+          for (int h = 0; h < 2; ++h) {
+            s2[h][j] = make_float2(b.x, b.x);
+            e2[h][j] = make_float2(b.y, b.y);
 #pragma unroll
-            for (int d = 0; d < DT; ++d) jd[i][j][d] = 0.f;
+            for (int d = 0; d < DT; ++d) jd2[h][j][d] = make_float2(0.f, 0.f);
           }
         }
-#pragma unroll 2
+#pragma unroll 4
         for (int c = 0; c < in; ++c) {
           const float4 ah = *reinterpret_cast<const float4*>(ahi + c * TV + vb);
           const float4 al = *reinterpret_cast<const float4*>(alo + c * TV + vb);
           float4 jv[DT];
 #pragma unroll
           for (int d = 0; d < DT; ++d) jv[d] = *reinterpret_cast<const float4*>(J + (c * DT + d) * TV + vb);
-          float2 w[4];
+          float2 w[kPtRows];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) w[j] = rb + j < H ? __ldg(Wt + (long long)c * H + rb + j) : make_float2(0.f, 0.f);
-          const float yh[4] = {ah.x, ah.y, ah.z, ah.w}, yl[4] = {al.x, al.y, al.z, al.w};
+          for (int j = 0; j < kPtRows; ++j) w[j] = rb + j < H ? __ldg(Wt + (long long)c * H + rb + j) : make_float2(0.f, 0.f);
+          const float2 yh[2] = {make_float2(ah.x, ah.y), make_float2(ah.z, ah.w)};
+          const float2 yl[2] = {make_float2(al.x, al.y), make_float2(al.z, al.w)};
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
+          for (int j = 0; j < kPtRows; ++j) {
+            const float2 xh = make_float2(w[j].x, w[j].x), xl = make_float2(w[j].y, w[j].y);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const float xh = w[j].x, xl = w[j].y;
-              const float pr = __fmul_rn(xh, yh[i]);
-              float er = fmaf(xh, yh[i], -pr);  // exact low part of the product
-              er = fmaf(xh, yl[i], er);         // cross terms of the low parts
-              er = fmaf(xl, yh[i], er);
-              const float t = __fadd_rn(s[i][j], pr);  // TwoSum: t + its error is exact
-              const float bb = __fsub_rn(t, s[i][j]);
-              e[i][j] += __fadd_rn(__fsub_rn(s[i][j], __fsub_rn(t, bb)), __fsub_rn(pr, bb)) + er;
-              s[i][j] = t;
+            for (int h = 0; h < 2; ++h) {
+              const float2 pr = __fmul2_rn(xh, yh[h]);
+              float2 er = __ffma2_rn(xh, yh[h], neg2(pr));  // exact low part of the product
+              er = __ffma2_rn(xh, yl[h], er);                // cross terms of the low parts
+              er = __ffma2_rn(xl, yh[h], er);
+              const float2 t = __fadd2_rn(s2[h][j], pr);     // TwoSum: t + its error is exact
+              const float2 bb = __fadd2_rn(t, neg2(s2[h][j]));
+              const float2 ts = __fadd2_rn(s2[h][j], neg2(__fadd2_rn(t, neg2(bb))));
+              e2[h][j] = __fadd2_rn(e2[h][j], __fadd2_rn(__fadd2_rn(ts, __fadd2_rn(pr, neg2(bb))), er));
+              s2[h][j] = t;
             }
-          }
 #pragma unroll
-          for (int d = 0; d < DT; ++d) {
-            const float g[4] = {jv[d].x, jv[d].y, jv[d].z, jv[d].w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int j = 0; j < 4; ++j) jd[i][j][d] = fmaf(w[j].x, g[i], jd[i][j][d]);
+            for (int d = 0; d < DT; ++d) {
+              jd2[0][j][d] = __ffma2_rn(xh, make_float2(jv[d].x, jv[d].y), jd2[0][j][d]);
+              jd2[1][j][d] = __ffma2_rn(xh, make_float2(jv[d].z, jv[d].w), jd2[1][j][d]);
+            }
           }
         }
       }
       __syncthreads();  // every input of the layer has been read
       if (busy) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int vv = vb + i;
-          const int nz = nzs[vv];
+        for (int j = 0; j < kPtRows; ++j) {
+          const int r = rb + j;
+          if (r >= H) continue;
+          const int entry = m + net.off[k] + r;
+          float zh[4], zo[4], g[DT][4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int r = rb + j;
-            if (r >= H) continue;
-            const ff z = ff_fast_two_sum(s[i][j], e[i][j]);
-            const int entry = m + net.off[k] + r;
+          for (int i = 0; i < 4; ++i) {
+            const float2 sp = s2[i >> 1][j], ep = e2[i >> 1][j];
+            const ff z = ff_fast_two_sum((i & 1) ? sp.y : sp.x, (i & 1) ? ep.y : ep.x);
+            zh[i] = z.hi;
+            zo[i] = z.lo;
+#pragma unroll
+            for (int d = 0; d < DT; ++d) g[d][i] = (i & 1) ? jd2[i >> 1][j][d].y : jd2[i >> 1][j][d].x;
+            const int vv = vb + i;
+            const int nz = nzs[vv];
             for (int q = 0; q < nz; ++q)
               if (zl[vv * DT + q] == entry) {
                 sgv[vv * DT + q] = static_cast<double>(z.hi) + static_cast<double>(z.lo);
 #pragma unroll
-                for (int d = 0; d < DT; ++d) sA[(vv * DT + q) * DT + d] = jd[i][j][d];
+                for (int d = 0; d < DT; ++d) sA[(vv * DT + q) * DT + d] = g[d][i];
               }
-            if (k < lmax) {
-              const bool act = ((sig[(entry >> 5) * TV + vv] >> (2 * (entry & 31))) & 3ull) == kPlus;
-              ahi[r * TV + vv] = act ? z.hi : 0.f;
-              alo[r * TV + vv] = act ? z.lo : 0.f;
+          }
+          if (k < lmax) {
+            bool act[4];
 #pragma unroll
-              for (int d = 0; d < DT; ++d) J[(r * DT + d) * TV + vv] = act ? jd[i][j][d] : 0.f;
-            }
+            for (int i = 0; i < 4; ++i)
+              act[i] = ((sig[(entry >> 5) * TV + vb + i] >> (2 * (entry & 31))) & 3ull) == kPlus;
+            *reinterpret_cast<float4*>(ahi + r * TV + vb) = make_float4(act[0] ? zh[0] : 0.f, act[1] ? zh[1] : 0.f,
+                                                                       act[2] ? zh[2] : 0.f, act[3] ? zh[3] : 0.f);
+            *reinterpret_cast<float4*>(alo + r * TV + vb) = make_float4(act[0] ? zo[0] : 0.f, act[1] ? zo[1] : 0.f,
+                                                                       act[2] ? zo[2] : 0.f, act[3] ? zo[3] : 0.f);
+#pragma unroll
+            for (int d = 0; d < DT; ++d)
+              *reinterpret_cast<float4*>(J + (r * DT + d) * TV + vb) =
+                  make_float4(act[0] ? g[d][0] : 0.f, act[1] ? g[d][1] : 0.f, act[2] ? g[d][2] : 0.f,
+                              act[3] ? g[d][3] : 0.f);
           }
         }
       }
