@@ -928,7 +928,8 @@ static void run_extract(pc_ctx* c, int L, const int32_t* widths, const double* p
   PC_CUDA(cudaMemsetAsync(c->cnt, 0, sizeof(Counters) * (n + 1), c->stream));
 
   // launch geometry
-  c->res_smem = (size_t)newton_ws_doubles(mw, D) * 8;
+  net.rd_batch = rd_batch_size(mw, D, net.S);
+  c->res_smem = rd_layout(net.rd_batch, mw, D, net.S).total;
   const int occ = occupancy_any(c);
   if (occ < 1) throw PcError(PC_ERR_INVALID, "persistent kernel does not fit on an SM");
   c->grid_persist = std::min(kMaxGrid, occ * c->num_sms);
@@ -1103,15 +1104,15 @@ static cudaError_t set_func_attributes_now() {
     const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) e = r;
   };
-  set((const void*)k_layer<double, false>, kNewtonSmemMax);
-  set((const void*)k_layer<float, false>, kNewtonSmemMax);
-  set((const void*)k_layer<float, true>, kNewtonSmemMax);
-  set((const void*)k_decide<double, false>, kNewtonSmemMax);
-  set((const void*)k_decide<float, false>, kNewtonSmemMax);
-  set((const void*)k_decide<float, true>, kNewtonSmemMax);
-  set((const void*)k_step<double, false>, kNewtonSmemMax);
-  set((const void*)k_step<float, false>, kNewtonSmemMax);
-  set((const void*)k_step<float, true>, kNewtonSmemMax);
+  set((const void*)k_layer<double, false>, kRdSmemMax);
+  set((const void*)k_layer<float, false>, kRdSmemMax);
+  set((const void*)k_layer<float, true>, kRdSmemMax);
+  set((const void*)k_decide<double, false>, kRdSmemMax);
+  set((const void*)k_decide<float, false>, kRdSmemMax);
+  set((const void*)k_decide<float, true>, kRdSmemMax);
+  set((const void*)k_step<double, false>, kRdSmemMax);
+  set((const void*)k_step<float, false>, kRdSmemMax);
+  set((const void*)k_step<float, true>, kRdSmemMax);
   set((const void*)k_polish<false>, kPolishSmemMax);
   set((const void*)k_polish<true>, kPolishSmemMax);
   {
@@ -1543,7 +1544,8 @@ extern "C" pc_status pc_extract_noalloc(int L, const int32_t* widths, const doub
     PC_CUDA(cudaMemsetAsync(base + kNaOffTable, 0xff, 32 * kNaMaxT, c.stream));
     PC_CUDA(cudaMemsetAsync(base + kNaOffFlags, 0, kNaFlagBytes, c.stream));
     PC_CUDA(cudaMemsetAsync(base + kNaOffCnt, 0, sizeof(Counters) * (nn + 1), c.stream));
-    c.res_smem = (size_t)newton_ws_doubles(mw, D) * 8;
+    net.rd_batch = rd_batch_size(mw, D, net.S);
+    c.res_smem = rd_layout(net.rd_batch, mw, D, net.S).total;
     occupancy_any(&c);
     c.grid_step = std::min(kMaxGrid, 2 * c.num_sms);
     k_init<<<1, 256, 0, c.stream>>>(net, make_state(&c));

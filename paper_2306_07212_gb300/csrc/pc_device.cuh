@@ -86,6 +86,7 @@ struct NetDesc {
   const double* fA;
   const double* fc;
   int debug_barrier;     // pc_options.debug_barrier_timeout
+  int rd_batch;          // vertices per batch of FP64 re-decisions (rd_batch_size)
 };
 
 struct Counters {        // 128 bytes

@@ -1,31 +1,24 @@
-// FP64 evaluation at the exact vertex, one CTA or one warp per vertex.
+// The Newton step to the exact vertex.
 //
 // A vertex lies on D zero entries (box facets or neuron pre-activations), all
 // affine on the vertex's own piece: the activation pattern is its stored sign
 // vector (a neuron is active iff its entry is +).  A forward pass from the
-// stored coordinates gives the value g (float64) and gradient (float32,
-// forward mode, D columns) of each zero entry; one Newton step on the D x D
-// system A dx = -g lands on the exact vertex: the system is affine, and the
-// step is small (the stored coordinates are FP32-accurate), so the float32
-// gradient adds only (1e-7 relative) x (step) to the result.  Used for
-//   * the filtered sign predicate: the value of neuron i at the exact vertex;
-//   * the coordinate polish: the exact vertex itself.
+// stored coordinates gives the value g and gradient (float32, forward mode,
+// D columns) of each zero entry; one Newton step on the D x D system
+// A dx = -g lands on the exact vertex: the system is affine, and the step is
+// small (the stored coordinates are FP32-accurate), so the float32 gradient
+// adds only (1e-7 relative) x (step) to the result.  Used for
+//   * the filtered sign predicate, values in float64 (redecide_batch,
+//     pc_phases.cuh): the values of layer l at the exact vertex;
+//   * the coordinate polish, values in float-float (newton_ff_warp below,
+//     and the tiled k_polish_tile): the exact vertex itself.
 #pragma once
 
 #include "pc_device.cuh"
 
 namespace pc {
 
-__host__ __device__ constexpr int newton_ws_doubles(int mw, int D) {
-  // a, an [mw]; J, Jn [mw x D] float; A [D x D], gv, jt [D]; misc; sign words;
-  // then, for the all-rows form, the last layer's values, sums of |terms|
-  // [mw] and gradients [mw x D] float
-  return 2 * mw + mw * D + D * D + 3 * D + 8 + kMaxWords + 2 * mw + (mw * D + 1) / 2;
-}
-
-// Upper bounds of the dynamic shared memory of the kernels that use the
-// Newton workspace; the launch attributes are set once to these constants.
-constexpr int kNewtonSmemMax = newton_ws_doubles(kMaxWidth, kMaxD) * 8;
+// Upper bound of the dynamic shared memory of the one-warp-per-vertex polish.
 constexpr int kPolishSmemMax = 220 * 1024;
 
 struct NewtonOut {
@@ -114,161 +107,6 @@ __device__ inline void newton_solve(const NetDesc& net, const State& st, long lo
   }
   for (int r = 0; r < D; ++r) o.dlt[r] = static_cast<double>(dl[r]);
   o.ok = 1;
-}
-
-// v: vertex; e_end: entries < e_end are processed (the zero set is taken among
-// them); l_last: last layer to evaluate (-1: the highest layer of the zero
-// set); i_target: neuron of layer l_last whose exact value is wanted (-1: none).
-// WARP = false: all threads of the CTA call it; WARP = true: all lanes of one
-// warp call it (ws, s_zl and out private to the warp).  ws holds
-// newton_ws_doubles(mw, D) doubles of shared memory.
-// ALL: every neuron of layer l_last is evaluated; its value at the stored
-// coordinates, its sum of |terms| and its gradient are left in the all-rows
-// arrays of ws (newton_all_rows), so that the caller can move each value to
-// the exact vertex with the Newton step out->dlt.
-template <bool WARP, bool ALL = false>
-__device__ void newton_group(const NetDesc& net, const State& st, long long v, int e_end, int l_last,
-                             int i_target, int mw, double* ws, int* s_zl, NewtonOut* out) {
-  const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
-  const int nth = WARP ? 32 : blockDim.x;
-  const int D = net.D, m = net.m;
-  const long long Vcap = st.Vcap;
-  double* a = ws;
-  double* an = a + mw;
-  float* J = reinterpret_cast<float*>(an + mw);
-  float* Jn = J + mw * D;
-  double* A = reinterpret_cast<double*>(Jn + mw * D);
-  double* gv = A + D * D;
-  double* jt = gv + D;
-  double* misc = jt + D;
-  uint64_t* sig = reinterpret_cast<uint64_t*>(misc + 8);  // the vertex's sign words
-  if (tid < 32) {
-    const int lane = tid;
-    const uint64_t word = lane < net.S ? st.SIG[(long long)lane * Vcap + v] : 0ull;
-    if (lane < net.S) sig[lane] = word;
-    const uint64_t zm = lane < net.S ? zero_mask(word, lane, e_end) : 0ull;
-    const int c = __popcll(zm);
-    int x = c;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    int k = x - c;
-    uint64_t mm = zm;
-    while (mm) {
-      const int bit = __ffsll((long long)mm) - 1;
-      if (k < kMaxD) s_zl[k] = lane * 32 + bit / 2;
-      ++k;
-      mm &= mm - 1;
-    }
-    if (lane == 31) s_zl[kMaxD] = x;
-  }
-  if (tid < D) {
-    a[tid] = st.X[(long long)tid * Vcap + v];
-    for (int dd = 0; dd < D; ++dd) J[tid * D + dd] = (tid == dd) ? 1.f : 0.f;
-  }
-  if (tid == 0) {
-    misc[0] = 0.0;
-    misc[1] = 0.0;
-  }
-  if (WARP) __syncwarp(); else __syncthreads();
-  const int nz = s_zl[kMaxD];
-  const int nzc = nz < D ? nz : D;
-  if (l_last < 0) {  // highest layer among the zero-set neurons
-    l_last = -1;
-    for (int q = 0; q < nzc; ++q) {
-      const int h = s_zl[q] - m;
-      if (h < 0) continue;
-      int l = 0;
-      while (l + 1 < net.L && h >= net.off[l + 1]) ++l;
-      if (l > l_last) l_last = l;
-    }
-  }
-  int in = D;
-  for (int k = 0; k <= l_last; ++k) {
-    const int H = net.w[k + 1];
-    const double* W = net.W64 + net.wofs[k];
-    const float* W32 = net.W32 + net.wofs[k];
-    const double* b = net.W64 + net.bofs[k];
-    int tpr = 16;
-    while (tpr > 1 && H * tpr > nth) tpr >>= 1;
-    const int rows = nth / tpr;
-    for (int r0 = 0; r0 < H; r0 += rows) {
-      const int r = r0 + tid / tpr, s = tid % tpr;
-      const int entry = m + net.off[k] + r;
-      int zpos = -1;
-      for (int q = 0; q < nzc; ++q)
-        if (s_zl[q] == entry) zpos = q;
-      const bool need = r < H && (k < l_last || r == i_target || zpos >= 0 || (ALL && k == l_last));
-      double acc = 0.0;
-      float sc = 0.f, jd[kMaxD];
-#pragma unroll
-      for (int dd = 0; dd < kMaxD; ++dd) jd[dd] = 0.f;
-      if (need) {
-        const double* wr = W + (long long)r * in;
-        const float* wr32 = W32 + (long long)r * in;
-        for (int c = s; c < in; c += tpr) {
-          const double av = a[c];
-          acc = fma(wr[c], av, acc);
-          const float w32 = wr32[c];
-          sc = fmaf(fabsf(w32), fabsf(static_cast<float>(av)), sc);
-#pragma unroll
-          for (int dd = 0; dd < kMaxD; ++dd)
-            if (dd < D) jd[dd] = fmaf(w32, J[c * D + dd], jd[dd]);
-        }
-      }
-      for (int o = tpr >> 1; o > 0; o >>= 1) {
-        acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        sc += __shfl_xor_sync(0xffffffffu, sc, o);
-#pragma unroll
-        for (int dd = 0; dd < kMaxD; ++dd) jd[dd] += __shfl_xor_sync(0xffffffffu, jd[dd], o);
-      }
-      if (need && s == 0) {
-        const double z = acc + b[r];
-        if (zpos >= 0) {
-          gv[zpos] = z;
-          for (int dd = 0; dd < D; ++dd) A[zpos * D + dd] = jd[dd];
-        }
-        if (k == l_last && r == i_target) {
-          misc[0] = z;
-          misc[1] = sc + fabs(b[r]);
-          for (int dd = 0; dd < D; ++dd) jt[dd] = jd[dd];
-        }
-        if (ALL && k == l_last) {
-          double* ov = reinterpret_cast<double*>(sig + kMaxWords);
-          ov[r] = z;
-          ov[mw + r] = sc + fabs(b[r]);
-          float* oj = reinterpret_cast<float*>(ov + 2 * mw);
-          for (int dd = 0; dd < D; ++dd) oj[r * D + dd] = jd[dd];
-        }
-        if (k < l_last) {
-          const bool act = ((sig[entry >> 5] >> (2 * (entry & 31))) & 3ull) == kPlus;
-          an[r] = act ? z : 0.0;
-          for (int dd = 0; dd < D; ++dd) Jn[r * D + dd] = act ? jd[dd] : 0.f;
-        }
-      }
-    }
-    if (WARP) __syncwarp(); else __syncthreads();
-    double* t0 = a; a = an; an = t0;
-    float* t1 = J; J = Jn; Jn = t1;
-    in = H;
-  }
-  if (net.fA != nullptr) {
-    domain_facet_rows(net, st, v, s_zl, nzc, tid, A, gv);
-    if (WARP) __syncwarp(); else __syncthreads();
-  }
-  if (tid == 0) {
-    NewtonOut o{};
-    o.nz = nz;
-    o.l_last = l_last;
-    o.z = misc[0];
-    o.scale = misc[1];
-    newton_solve(net, st, v, s_zl, nz, A, gv, o);
-    if (o.ok && i_target >= 0)
-      for (int dd = 0; dd < D; ++dd) o.z += jt[dd] * o.dlt[dd];
-    *out = o;
-  }
-  if (WARP) __syncwarp(); else __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -419,26 +257,6 @@ __device__ void newton_ff_warp(const NetDesc& net, const State& st, const float2
     *out = o;
   }
   __syncwarp();
-}
-
-__device__ __forceinline__ void newton_cta(const NetDesc& net, const State& st, long long v, int e_end,
-                                           int l_last, int i_target, int mw, double* ws, int* s_zl,
-                                           NewtonOut* out) {
-  newton_group<false>(net, st, v, e_end, l_last, i_target, mw, ws, s_zl, out);
-}
-
-// The all-rows arrays of a newton_group<., true> workspace: values at the
-// stored coordinates, sums of |terms| (both mw doubles) and gradients
-// (mw x D floats) of the neurons of layer l_last.
-struct NewtonRows {
-  const double* val;
-  const double* scale;
-  const float* grad;
-};
-__device__ __forceinline__ NewtonRows newton_all_rows(const NetDesc& net, const double* ws, int mw) {
-  const int D = net.D;
-  const double* ov = ws + 2 * mw + mw * D + D * D + 2 * D + 8 + kMaxWords;  // just after the sign words
-  return {ov, ov + mw, reinterpret_cast<const float*>(ov + 2 * mw)};
 }
 
 }  // namespace pc

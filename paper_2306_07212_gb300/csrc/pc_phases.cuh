@@ -30,7 +30,7 @@
 //
 // A new vertex whose value for a later neuron of the layer is within the FP32
 // filter is re-decided in FP64 by its CTA right after it is created, before
-// anything reads that sign.
+// anything reads that sign (the round's flagged vertices of a CTA together).
 #pragma once
 
 #include "pc_device.cuh"
@@ -58,8 +58,6 @@ struct Smem {
   int zlist[kWarps][16];
   float nrl[3 * kMaxWidth];            // the layer's per-neuron norms (NetDesc::nrm)
   int nrl_layer;                       // layer staged in nrl, -1: none
-  int nzl[kMaxD + 2];
-  NewtonOut nout;
   long long acc[4];
 };
 
@@ -120,27 +118,186 @@ __device__ __forceinline__ void warp_append(int c, const int4* ent, int4* list, 
 }
 
 // ---------------------------------------------------------------------------
-// FP64 re-decision of vertex v's values z_j, j >= j_from, of layer l that lie
-// within the FP32 filter: all threads of the CTA evaluate layer l at the exact
-// vertex (Newton step on its zero set among the entries < e_end) and write
-// back each filtered value with its FP64 sign.
+// FP64 re-decision of the values z_j, j >= j_from, of layer l that lie within
+// the FP32 filter, for a batch of P vertices at once (the CTA's queued new
+// vertices).  Each vertex's layer-l values are evaluated at its exact position:
+// a forward pass in float64 from its stored coordinates through layers 0..l
+// on its own piece (activation pattern = its sign words; gradients in float32,
+// forward mode), then one Newton step on its zero set among the entries
+// < e_end moves every value to the exact vertex, z + grad . dx (the step is
+// small, so the float32 gradient adds only ~1e-7 of it).  Each filtered value
+// is written back with its FP64 sign.  The forward pass runs over all
+// (vertex, neuron) pairs of the batch together, tpr threads per pair, so the
+// batch costs one pass of per-layer latency instead of one per vertex.
+// Workspace (dynamic shared memory), rd_layout(P, mw, D, S) bytes:
+struct RdLayout {
+  size_t a, an, A, gv, dlt, sig, J, Jn, sc, zl, nz, ok, total;
+};
+__host__ __device__ inline RdLayout rd_layout(int P, int mw, int D, int S) {
+  RdLayout r{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += (bytes + 15) / 16 * 16;
+    return at;
+  };
+  r.a = take((size_t)P * mw * 8);       // activations (float64) [P][mw]
+  r.an = take((size_t)P * mw * 8);      // next layer's
+  r.A = take((size_t)P * D * D * 8);    // Newton rows [P][D][D]
+  r.gv = take((size_t)P * D * 8);       // their values [P][D]
+  r.dlt = take((size_t)P * D * 8);      // Newton steps [P][D]
+  r.sig = take((size_t)P * S * 8);      // sign words [P][S]
+  r.J = take((size_t)P * mw * D * 4);   // gradients (float) [P][mw][D]
+  r.Jn = take((size_t)P * mw * D * 4);
+  r.sc = take((size_t)P * mw * 4);      // sums of |terms| of layer l [P][mw]
+  r.zl = take((size_t)P * D * 4);       // zero entries [P][D]
+  r.nz = take((size_t)P * 4);           // zero entries found
+  r.ok = take((size_t)P * 4);           // Newton step taken
+  r.total = o;
+  return r;
+}
+constexpr int kRdSmemBudget = 48 * 1024;  // shared memory for a batch
+constexpr int kRdSmemMax = 64 * 1024;     // launch attribute of the kernels that hold it
+
+// Vertices per batch: all warps' new vertices of a round (kWarps), fewer
+// when the workspace would exceed the budget (wide layers, large D).
+__host__ inline int rd_batch_size(int mw, int D, int S) {
+  int P = kWarps;
+  while (P > 1 && rd_layout(P, mw, D, S).total > (size_t)kRdSmemBudget) --P;
+  return P;
+}
+
 template <typename ZT>
-__device__ void redecide_cta(const NetDesc& net, const State& st, long long v, int l, int e_end, int j_from,
-                             int mw, double* ws, Smem& sm) {
-  newton_group<false, true>(net, st, v, e_end, l, -1, mw, ws, sm.nzl, &sm.nout);
-  const NewtonRows rows = newton_all_rows(net, ws, mw);
-  const int H = net.w[l + 1], n0 = net.off[l], D = net.D;
+__device__ void redecide_batch(const NetDesc& net, const State& st, const long long* vs, int P, int l,
+                                            int e_end, int j_from, int mw, unsigned char* ws) {
+  const int D = net.D, S = net.S, m = net.m;
   const long long Vcap = st.Vcap;
+  const RdLayout L = rd_layout(P, mw, D, S);
+  double* a = reinterpret_cast<double*>(ws + L.a);
+  double* an = reinterpret_cast<double*>(ws + L.an);
+  double* A = reinterpret_cast<double*>(ws + L.A);
+  double* gv = reinterpret_cast<double*>(ws + L.gv);
+  double* dlt = reinterpret_cast<double*>(ws + L.dlt);
+  uint64_t* sig = reinterpret_cast<uint64_t*>(ws + L.sig);
+  float* J = reinterpret_cast<float*>(ws + L.J);
+  float* Jn = reinterpret_cast<float*>(ws + L.Jn);
+  float* sc = reinterpret_cast<float*>(ws + L.sc);
+  int* zl = reinterpret_cast<int*>(ws + L.zl);
+  int* nzs = reinterpret_cast<int*>(ws + L.nz);
+  int* oks = reinterpret_cast<int*>(ws + L.ok);
+  for (int t = threadIdx.x; t < P * S; t += blockDim.x) {
+    const int q = t / S, w = t - q * S;
+    sig[t] = st.SIG[(long long)w * Vcap + vs[q]];
+  }
+  for (int t = threadIdx.x; t < P * D; t += blockDim.x) {
+    const int q = t / D, d = t - q * D;
+    a[q * mw + d] = st.X[(long long)d * Vcap + vs[q]];
+    for (int dd = 0; dd < D; ++dd) J[(q * mw + d) * D + dd] = d == dd ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < P; q += blockDim.x) {  // zero set among the entries < e_end
+    int nz = 0;
+    for (int w = 0; w < S; ++w) {
+      uint64_t zm = zero_mask(sig[q * S + w], w, e_end);
+      while (zm) {
+        const int bit = __ffsll((long long)zm) - 1;
+        if (nz < D) zl[q * D + nz] = w * 32 + bit / 2;
+        ++nz;
+        zm &= zm - 1;
+      }
+    }
+    nzs[q] = nz;
+  }
+  __syncthreads();
+  int in = D;
+  for (int k = 0; k <= l; ++k) {
+    const int H = net.w[k + 1];
+    const double* W = net.W64 + net.wofs[k];  // [H][in]
+    const float* W32 = net.W32 + net.wofs[k];
+    const double* b = net.W64 + net.bofs[k];
+    const int pairs = P * H;
+    int tpr = 32;
+    while (tpr > 1 && pairs * tpr > (int)blockDim.x) tpr >>= 1;
+    const int per = blockDim.x / tpr;
+    for (int p0 = 0; p0 < pairs; p0 += per) {
+      const int pr = p0 + threadIdx.x / tpr, s = threadIdx.x % tpr;
+      const bool valid = pr < pairs;
+      const int q = valid ? pr / H : 0, r = valid ? pr - q * H : 0;
+      double acc = 0.0;
+      float scl = 0.f, jd[kMaxD];
+#pragma unroll
+      for (int dd = 0; dd < kMaxD; ++dd) jd[dd] = 0.f;
+      if (valid) {
+        const double* wr = W + (long long)r * in;
+        const float* wr32 = W32 + (long long)r * in;
+        const double* aq = a + q * mw;
+        const float* Jq = J + q * mw * D;
+        for (int c = s; c < in; c += tpr) {
+          const double av = aq[c];
+          acc = fma(wr[c], av, acc);
+          const float w32 = wr32[c];
+          scl = fmaf(fabsf(w32), fabsf(static_cast<float>(av)), scl);
+#pragma unroll
+          for (int dd = 0; dd < kMaxD; ++dd)
+            if (dd < D) jd[dd] = fmaf(w32, Jq[c * D + dd], jd[dd]);
+        }
+      }
+      for (int o = tpr >> 1; o > 0; o >>= 1) {  // the tpr lanes of a pair are aligned
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        scl += __shfl_xor_sync(0xffffffffu, scl, o);
+#pragma unroll
+        for (int dd = 0; dd < kMaxD; ++dd) jd[dd] += __shfl_xor_sync(0xffffffffu, jd[dd], o);
+      }
+      if (valid && s == 0) {
+        const double z = acc + b[r];
+        const int entry = m + net.off[k] + r;
+        const int nzc = nzs[q] < D ? nzs[q] : D;
+        for (int qq = 0; qq < nzc; ++qq)
+          if (zl[q * D + qq] == entry) {
+            gv[q * D + qq] = z;
+            for (int dd = 0; dd < D; ++dd) A[(q * D + qq) * D + dd] = jd[dd];
+          }
+        if (k < l) {
+          const bool act = ((sig[q * S + (entry >> 5)] >> (2 * (entry & 31))) & 3ull) == kPlus;
+          an[q * mw + r] = act ? z : 0.0;
+          for (int dd = 0; dd < D; ++dd) Jn[(q * mw + r) * D + dd] = act ? jd[dd] : 0.f;
+        } else {
+          an[q * mw + r] = z;
+          sc[q * mw + r] = scl + fabsf(static_cast<float>(b[r]));
+          for (int dd = 0; dd < D; ++dd) Jn[(q * mw + r) * D + dd] = jd[dd];
+        }
+      }
+    }
+    __syncthreads();
+    double* t0 = a; a = an; an = t0;
+    float* t1 = J; J = Jn; Jn = t1;
+    in = H;
+  }
+  for (int q = threadIdx.x; q < P; q += blockDim.x) {  // the Newton step of each vertex
+    int* zq = zl + q * D;
+    const int nzc = nzs[q] < D ? nzs[q] : D;
+    if (net.fA != nullptr)
+      for (int qq = 0; qq < nzc; ++qq) domain_facet_rows(net, st, vs[q], zq, nzc, qq, A + q * D * D, gv + q * D);
+    NewtonOut o{};
+    newton_solve(net, st, vs[q], zq, nzs[q], A + q * D * D, gv + q * D, o);
+    oks[q] = o.ok;
+    for (int d = 0; d < D; ++d) dlt[q * D + d] = o.ok ? o.dlt[d] : 0.0;
+  }
+  __syncthreads();
+  // layer l's values (a), gradients (J) and sums of |terms| (sc): decide
+  const int H = net.w[l + 1], n0 = net.off[l];
   ZT* Z = static_cast<ZT*>(st.Z[l]);
-  const float esc = st.esc[v];
-  for (int j = j_from + threadIdx.x; j < H; j += blockDim.x) {
+  const int nj = H - j_from;
+  for (int t = threadIdx.x; t < P * nj; t += blockDim.x) {
+    const int q = t / nj, j = j_from + (t - q * nj);
+    const long long v = vs[q];
     const float z32 = static_cast<float>(Z[(long long)j * Vcap + v]);
-    const float est = net.nrm[3 * (n0 + j)] * esc + 2.9802322e-8f * net.nrm[3 * (n0 + j) + 1];
+    const float est = net.nrm[3 * (n0 + j)] * st.esc[v] + 2.9802322e-8f * net.nrm[3 * (n0 + j) + 1];
     if (!(fabsf(z32) <= net.kappa_sel * est)) continue;
-    double zs = rows.val[j];
-    if (sm.nout.ok)
-      for (int d = 0; d < D; ++d) zs += static_cast<double>(rows.grad[j * D + d]) * sm.nout.dlt[d];
-    const bool und = !sm.nout.ok || fabs(zs) <= 1e-12 * rows.scale[j];
+    double zs = a[q * mw + j];
+    if (oks[q])
+      for (int d = 0; d < D; ++d) zs += static_cast<double>(J[(q * mw + j) * D + d]) * dlt[q * D + d];
+    const bool und = !oks[q] || fabs(zs) <= 1e-12 * sc[q * mw + j];
     const bool minus = zs < 0.0;
     if (!(fabsf(z32) <= net.kappa * est)) {  // audit band: record a wrong FP32 sign, change nothing
       if ((z32 < 0.f) != minus && !und) {
@@ -163,12 +320,16 @@ __device__ void redecide_cta(const NetDesc& net, const State& st, long long v, i
   __syncthreads();
 }
 
-// Re-decides the CTA's queued vertices one after another and empties the queue.
+// Re-decides the CTA's queued vertices in batches of net.rd_batch and empties
+// the queue.
 template <typename ZT>
 __device__ void drain_pending(const NetDesc& net, const State& st, int l, int e_end, int j_from, int mw, double* ws,
                               Smem& sm) {
   const int np = sm.npend;
-  for (int q = 0; q < np; ++q) redecide_cta<ZT>(net, st, sm.pend[q], l, e_end, j_from, mw, ws, sm);
+  for (int q0 = 0; q0 < np; q0 += net.rd_batch) {
+    const int P = np - q0 < net.rd_batch ? np - q0 : net.rd_batch;
+    redecide_batch<ZT>(net, st, sm.pend + q0, P, l, e_end, j_from, mw, reinterpret_cast<unsigned char*>(ws));
+  }
   __syncthreads();
   if (threadIdx.x == 0) sm.npend = 0;
   __syncthreads();
