@@ -42,12 +42,16 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) per k_layer launch of the mixed-precision torus
-# extraction, from one ncu capture of the k_layer launches of one extraction,
-# and a hash of the kernel sources it was taken with: the figure is reported
-# only while the sources are unchanged (else traffic is null).
-K_LAYER_DRAM = {"bytes_per_launch": None, "sources_sha16": None}
-KERNEL_SOURCES = ("pc_phases.cuh", "pc_core.cu", "pc_device.cuh", "pc_newton.cuh")
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) per launch,
+# averaged over the launches of one steady-state mixed-precision extraction,
+# and a hash of the kernel sources they were taken with: the figures are
+# reported only while the sources are unchanged (else traffic is null).
+#   k_layer_torus      the D=3 torus workload, 5 k_layer launches
+#   k_layer_d5w40      the D=5 width-40 counting-sweep net (seed 0), 5 launches
+#   k_gemm_tc2_d5w40   the same net's 4 tensor-core layer products
+KERNEL_DRAM = {"sources_sha16": "e83fb753b5871c0b", "k_layer_torus": 183403264, "k_layer_d5w40": 30201796761,
+               "k_gemm_tc2_d5w40": 1222340864}
+KERNEL_SOURCES = ("pc_phases.cuh", "pc_core.cu", "pc_device.cuh", "pc_newton.cuh", "pc_gemm_tc.cu", "pc_polish.cu")
 
 METRIC = "vertices+edges/s at D=3 (torus 3-64x4-1, box [-1,1]^3)"
 UNIT = "(V+E)/s"
@@ -119,6 +123,16 @@ class ClockSampler:
 
 
 # -- algorithmic bytes of the neuron loop -------------------------------------
+
+def kernel_traffic(key: str, precision: str) -> dict:
+    """The captured DRAM bytes per launch (KERNEL_DRAM), or null when the
+    kernel sources changed since the capture or the precision differs."""
+    if precision == "mixed" and KERNEL_DRAM["sources_sha16"] == kernel_sources_sha16() and KERNEL_DRAM[key]:
+        return {"traffic": KERNEL_DRAM[key],
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, averaged over the "
+                                  "launches of one steady-state extraction of this workload"}
+    return {"traffic": None, "traffic_source": "not captured for these kernel sources"}
+
 
 def kernel_sources_sha16() -> str:
     import hashlib
@@ -298,13 +312,7 @@ def run_ours(args, rank, world, local_rank):
     roofline = loop_roofline(layer_bytes, loop_avg, peak, peak_kind)
     roofline["share_of_step"] = round(float(loop_avg.sum() / statistics.mean(step_ms)), 3)
     roofline["forward_product_ms_per_step"] = round(float(gemm_avg.sum()), 4)
-    if args.precision == "mixed" and K_LAYER_DRAM["sources_sha16"] == kernel_sources_sha16():
-        roofline["traffic"] = K_LAYER_DRAM["bytes_per_launch"]
-        roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the k_layer launches of "
-                                      "one extraction of this workload, per launch")
-    else:
-        roofline["traffic"] = None
-        roofline["traffic_source"] = "not captured for these kernel sources"
+    roofline.update(kernel_traffic("k_layer_torus", args.precision))
     out = None
     if rank == 0:
         cpu = cpu_baseline(net, box) if world == 1 else None
@@ -428,6 +436,7 @@ def run_large(device: int, args, flush, peak, peak_kind) -> dict:
     loop_ms = np.mean(np.stack(loops), axis=0)
     gemm_ms = np.mean(np.stack(gemms), axis=0)
     roof = loop_roofline(neuron_loop_bytes(net, stats, args.precision), loop_ms, peak, peak_kind)
+    roof.update(kernel_traffic("k_layer_d5w40", args.precision))
     tf32 = measure_tf32_tflops(device)
     gb = gemm_bytes_flops(net, stats, args.precision)[1:]  # layers 2.. run on the tensor cores
     gms = gemm_ms[1:]
@@ -439,12 +448,14 @@ def run_large(device: int, args, flush, peak, peak_kind) -> dict:
             "value": round((c["nV"] + c["nE"]) / (float(np.median(step)) / 1e3), 1), "unit": UNIT,
             "loop_ms": round(float(np.sum(loop_ms)), 2), "forward_product_ms": round(float(np.sum(gemm_ms)), 2),
             "polish_ms": round(polish_ms, 2), "roofline": roof,
-            "gemm_roofline": {"kernel": "k_gemm_tc (layers 2-5)", "bound": "hbm",
+            "gemm_roofline": {"kernel": "k_gemm_tc2 (layers 2-5)", "bound": "hbm",
                               "achieved": round(gbytes / gt / 1e9, 2), "peak": peak, "unit": "GB/s",
                               "frac": round(gbytes / gt / 1e9 / peak, 4),
                               "tensor_tflops": round(gflops / gt / 1e12, 2), "tf32_peak_tflops": tf32,
                               "tensor_frac": round(gflops / gt / 1e12 / tf32, 4) if tf32 else None,
-                              "peak_source": "hbm " + peak_kind + "; TF32 measured in this run (torch.matmul 8192^3)"}}
+                              "bytes_per_launch_avg": int(gbytes / len(gb)),
+                              "peak_source": "hbm " + peak_kind + "; TF32 measured in this run (torch.matmul 8192^3)",
+                              **kernel_traffic("k_gemm_tc2_d5w40", args.precision)}}
 
 
 def run_serving_pair(args) -> dict:

@@ -204,3 +204,13 @@ def test_traffic_is_tied_to_the_kernel_sources():
     sha = bench.kernel_sources_sha16()
     assert len(sha) == 16 and all(ch in "0123456789abcdef" for ch in sha)
     assert sha == bench.kernel_sources_sha16()
+
+
+def test_captured_traffic_is_reported_only_for_its_sources(monkeypatch):
+    key = "k_layer_torus"
+    monkeypatch.setitem(bench.KERNEL_DRAM, key, 123)
+    monkeypatch.setitem(bench.KERNEL_DRAM, "sources_sha16", bench.kernel_sources_sha16())
+    assert bench.kernel_traffic(key, "mixed")["traffic"] == 123
+    assert bench.kernel_traffic(key, "fp64")["traffic"] is None  # captured in mixed precision only
+    monkeypatch.setitem(bench.KERNEL_DRAM, "sources_sha16", "0" * 16)
+    assert bench.kernel_traffic(key, "mixed")["traffic"] is None
