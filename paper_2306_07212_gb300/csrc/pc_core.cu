@@ -1123,6 +1123,10 @@ static cudaError_t set_func_attributes_now() {
     const cudaError_t r = pc_polish_tile_set_attributes();
     if (e == cudaSuccess) e = r;
   }
+  {
+    const cudaError_t r = pc_prune_set_attributes();
+    if (e == cudaSuccess) e = r;
+  }
   pc_adjoint_set_attributes();
   return e;
 }

@@ -27,6 +27,7 @@ void pc_poset_release(pc_ctx* c);
 // pruning during subdivision (pc_prune.cu)
 void pc_prune_edges(pc_ctx* c, const pc::State& st, int l);
 void pc_prune_vertices(pc_ctx* c);
+cudaError_t pc_prune_set_attributes();
 
 // tcgen05 layer-start product (pc_gemm_tc.cu)
 bool pc_gemm_tc_eligible(const pc::NetDesc& net, int l);

@@ -538,15 +538,15 @@ __device__ void phase_scan0(const NetDesc& net, const State& st, int l, Smem& sm
 }
 
 // ---------------------------------------------------------------------------
-// Whole-warp check (inline pairing) that the 2-face key of split k2 (payload
-// r2 = 2 * zero ordinal + minus) equals F, where lane w holds word w of this
+// Whole-warp check (inline pairing) that the 2-face key of the new vertex
+// nV + k2 (payload r2 = 2 * zero ordinal + minus) equals F, where lane w holds word w of this
 // splitting edge's sign vector s0 and F is s0 with word wj replaced by Fw.
 // The partner's face is rebuilt from its new vertex's sign words, which the
 // partner wrote (and fenced) before it inserted its key.  All lanes call it.
 __device__ __forceinline__ bool warp_face_matches(const State& st, long long k2, int r2, int e, int S, uint64_t s0,
                                                   int wj, uint64_t Fw, long long nV, long long total, int n) {
   const int lane = threadIdx.x & 31;
-  if (k2 < 0 || k2 >= total) {  // a payload that no split of this step wrote
+  if (k2 < 0 || k2 >= total) {  // a payload that no new vertex of this step wrote
     if (lane == 0) report_corrupt(st.g, 5, n, k2, total, r2);
     return false;
   }
@@ -714,10 +714,18 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
     const long long k = rd * Wt + k_first;  // splits dealt over the CTAs first
     const int4 sg_this = sg_next;
     if (k + Wt < total) sg_next = lcur[k + Wt];  // the next round's, loaded during this one
+    // The round's new vertices are numbered CTA by CTA: CTA b holds entries
+    // w G + b of the round (w < n_b = rq + [b < rr]) and gives them the
+    // consecutive offsets b rq + min(b, rr) + w, a bijection onto the
+    // round's [0, rem), so each CTA writes whole sectors of the value,
+    // coordinate and sign rows.
+    const long long rem = total - rd * Wt < Wt ? total - rd * Wt : Wt;
+    const long long rq = rem / G, rr = rem - rq * G;
+    const long long voff = rd * Wt + blockIdx.x * rq + (blockIdx.x < rr ? blockIdx.x : rr) + warp;
     // ---- part A: the new vertex (step (4)) ----
     bool okA = false, pend = false, bad = false;
     int32_t ed = 0, p = 0, q = 0;
-    const int32_t v0 = int32_t(nV + k);
+    const int32_t v0 = int32_t(nV + voff);
     uint64_t s0 = 0, zm = 0;
     ZT zpn = ZT(0), zqn = ZT(0), z0n = ZT(0);  // values at neuron i + 1
     if (k < total) {
@@ -932,7 +940,7 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
         // (k_verify_pairs) from the two new vertices' sign vectors.
         if (has_key) {
           if (h == kEmpty) h = kEmpty - 1;
-          const unsigned long long mine = (uint64_t(k) * R + uint64_t(lane)) | (m0n ? (1ull << 62) : 0ull);
+          const unsigned long long mine = (uint64_t(voff) * R + uint64_t(lane)) | (m0n ? (1ull << 62) : 0ull);
           unsigned long long* tb = reinterpret_cast<unsigned long long*>(table);
           for (long long probes = 0;; ++probes) {
             if (probes > tneed) {
@@ -964,7 +972,7 @@ __device__ bool phase_step(const NetDesc& net, const State& st, int l, int i, Sm
         __threadfence();
         __syncwarp();
         const uint32_t tag = uint32_t(h >> 32);
-        const uint64_t mine = has_key ? ((uint64_t(tag) << 32) | (uint64_t(k) * R + uint64_t(lane))) : 0ull;
+        const uint64_t mine = has_key ? ((uint64_t(tag) << 32) | (uint64_t(voff) * R + uint64_t(lane))) : 0ull;
         bool active = has_key;
         long long probes = 0;
         while (__any_sync(0xffffffffu, active)) {

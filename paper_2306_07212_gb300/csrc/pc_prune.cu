@@ -2,10 +2,11 @@
 // extracting the level set of the output neuron without the rest of the
 // complex.
 //
-// After each layer l but the last, every current vertex gets its signs
-// w.r.t. all future neurons (layers l+1 .. L-1) from an FP64 forward pass at
-// its coordinates: the stored activation pattern for layers <= l, the ReLU of
-// the computed values beyond.  An edge whose two vertices have the same
+// After each layer l but the last, every current vertex with an edge gets
+// its signs w.r.t. all future neurons (layers l+1 .. L-1) from a forward pass
+// at its coordinates (float-float, its error far inside the uncertainty band
+// below): the stored activation pattern for layers <= l, the ReLU of the
+// computed values beyond.  An edge whose two vertices have the same
 // future signs is crossed by no future folded hyperplane (along the edge the
 // next layer is affine, and so are the later ones while no earlier neuron
 // splits it), so it cannot meet the output's zero set: it is dropped.  A
@@ -37,11 +38,33 @@ __device__ __forceinline__ bool g_stopped(const Global* g) {  // once per CTA
                                                 *(volatile const int*)&g->halted_at >= 0)) != 0;
 }
 
-// FP64 forward pass of vertex v (one per warp) through the rest of the net.
+// used[v] = 1 for every endpoint of the edges present after layer l.
+__global__ void k_mark_edge_ends(NetDesc net, State st, int l, unsigned char* used) {
+  if (cta_stopped(st)) return;
+  const Counters* c = st.cnt + net.off[l + 1];
+  const long long nE = c->nE_before + c->nsplit + c->npairs;
+  const long long nV = c->nV_before + c->nsplit;
+  if (nE < 0 || nE > st.Ecap) return;  // k_edge_keep reports it
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += (long long)gridDim.x * blockDim.x) {
+    const int u = st.EU[e], w = st.EW[e];
+    if (u >= 0 && u < nV) used[u] = 1;
+    if (w >= 0 && w < nV) used[w] = 1;
+  }
+}
+
+// Forward pass of vertex v (one per warp) through the rest of the net, for
+// the vertices that still have an edge (used; the others are never read),
+// in float-float arithmetic (Dot2 as in the polish: exact products by FMA,
+// TwoSum of the running sum, error terms in a float; weights as (head,
+// remainder) pairs, W^T layout so that the lanes' rows are contiguous).
 // fut: Wf 32-bit words per vertex (bit f = 1 iff future neuron f is +);
-// unc: 1 if a future value is within 1e-9 of its sum of |terms|.
+// unc: 1 if a future value is within 1e-9 of its sum of |terms|.  The
+// float-float error, ~(n u)^2 of that sum per layer (u = 2^-24; 1.5e-11 for
+// 64 inputs), is far inside the band, so every sign outside it is the exact
+// one, and a vertex with a value inside it keeps its edges.
 __global__ void __launch_bounds__(32 * kPruneWarps) k_future_signs(NetDesc net, State st, int l, int mw, int Wf,
-                                                                   uint32_t* fut, unsigned char* unc) {
+                                                                   const unsigned char* used, uint32_t* fut,
+                                                                   unsigned char* unc) {
   extern __shared__ double psh[];
   if (cta_stopped(st)) return;
   const Counters* c = st.cnt + net.off[l + 1];
@@ -52,43 +75,63 @@ __global__ void __launch_bounds__(32 * kPruneWarps) k_future_signs(NetDesc net, 
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* buf = psh + (long long)warp * (2 * mw + Wf);
+  float* fbuf = reinterpret_cast<float*>(buf);                  // a (hi, lo), next (hi, lo): 4 mw floats
   uint32_t* words = reinterpret_cast<uint32_t*>(buf + 2 * mw);  // Wf words (room for 2 Wf)
   const long long Vcap = st.Vcap;
   const int D = net.D, m = net.m, fbase = net.off[l + 1];
   for (long long v = (long long)blockIdx.x * kPruneWarps + warp; v < nV; v += (long long)gridDim.x * kPruneWarps) {
-    double* a = buf;
-    double* an = buf + mw;
+    if (!used[v]) continue;  // warp-uniform
+    float* ahi = fbuf;
+    float* alo = fbuf + mw;
+    float* nhi = fbuf + 2 * mw;
+    float* nlo = fbuf + 3 * mw;
     for (int w = lane; w < Wf; w += 32) words[w] = 0u;
-    if (lane < D) a[lane] = st.X[(long long)lane * Vcap + v];
+    if (lane < D) {
+      const double x = st.X[(long long)lane * Vcap + v];
+      ahi[lane] = static_cast<float>(x);
+      alo[lane] = static_cast<float>(x - static_cast<double>(ahi[lane]));
+    }
     __syncwarp();
     int in = D;
     bool uncertain = false;
     for (int k = 0; k < net.L; ++k) {
       const int H = net.w[k + 1];
-      const double* W = net.W64 + net.wofs[k];
-      const double* b = net.W64 + net.bofs[k];
+      const float2* Wt = net.WT2 + net.wofs[k];  // [in][H]
       for (int r = lane; r < H; r += 32) {
-        double z = b[r], sc = fabs(b[r]);
-        const double* wr = W + (long long)r * in;
+        const float2 bj = net.WT2[net.bofs[k] + r];
+        float s = bj.x, e = bj.y, sc = fabsf(bj.x);
         for (int q = 0; q < in; ++q) {
-          z = fma(wr[q], a[q], z);
-          sc += fabs(wr[q] * a[q]);
+          const float2 w = Wt[(long long)q * H + r];
+          const float yh = ahi[q], yl = alo[q];
+          const float pr = __fmul_rn(w.x, yh);
+          float er = fmaf(w.x, yh, -pr);  // exact low part of the product
+          er = fmaf(w.x, yl, er);         // cross terms of the low parts
+          er = fmaf(w.y, yh, er);
+          const float t = __fadd_rn(s, pr);  // TwoSum: t + its error is exact
+          const float bb = __fsub_rn(t, s);
+          e += __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(pr, bb)) + er;
+          s = t;
+          sc = fmaf(fabsf(w.x), fabsf(yh), sc);
         }
+        const float zh = __fadd_rn(s, e);  // the float-float value zh + zl
+        const float zl = __fsub_rn(e, __fsub_rn(zh, s));
         const int entry = m + net.off[k] + r;
+        bool act;
         if (k <= l) {
           const uint64_t word = st.SIG[(long long)(entry >> 5) * Vcap + v];
-          an[r] = (((word >> (2 * (entry & 31))) & 3ull) == kPlus) ? z : 0.0;
+          act = ((word >> (2 * (entry & 31))) & 3ull) == kPlus;
         } else {
-          if (fabs(z) <= 1e-9 * sc) uncertain = true;
+          if (fabsf(zh) <= 1e-9f * sc) uncertain = true;
           const int f = net.off[k] + r - fbase;
-          if (z > 0.0) atomicOr(&words[f >> 5], 1u << (f & 31));
-          an[r] = z > 0.0 ? z : 0.0;
+          act = zh > 0.f;
+          if (act) atomicOr(&words[f >> 5], 1u << (f & 31));
         }
+        nhi[r] = act ? zh : 0.f;
+        nlo[r] = act ? zl : 0.f;
       }
       __syncwarp();
-      double* t = a;
-      a = an;
-      an = t;
+      float* t0 = ahi; ahi = nhi; nhi = t0;
+      float* t1 = alo; alo = nlo; nlo = t1;
       in = H;
     }
     const unsigned any_unc = __ballot_sync(0xffffffffu, uncertain);
@@ -243,6 +286,13 @@ int grid_of(long long n) { return static_cast<int>(std::max<long long>(1, std::m
 
 }  // namespace
 
+// Upper bound of k_future_signs' dynamic shared memory (widths <= kMaxWidth,
+// at most kMaxEntries future neurons), set once as its launch attribute.
+cudaError_t pc_prune_set_attributes() {
+  const int bytes = static_cast<int>(sizeof(double) * kPruneWarps * (2 * kMaxWidth + kMaxEntries / 32));
+  return cudaFuncSetAttribute(k_future_signs, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 // Enqueues the edge pruning after layer l (l < L - 1) on the context's
 // stream.  Temporaries are allocated here and freed in stream order.
 void pc_prune_edges(pc_ctx* c, const State& st, int l) {
@@ -254,6 +304,7 @@ void pc_prune_edges(pc_ctx* c, const State& st, int l) {
   const int nblocks = static_cast<int>((E + kCompactBlock - 1) / kCompactBlock);
   void* fut = ctx_alloc(c, sizeof(uint32_t) * Wf * V);
   void* unc = ctx_alloc(c, V);
+  void* used = ctx_alloc(c, V);
   void* keep = ctx_alloc(c, sizeof(int) * E);
   void* counts = ctx_alloc(c, sizeof(int) * (nblocks + 1));
   void* tU = ctx_alloc(c, sizeof(int32_t) * E);
@@ -262,13 +313,14 @@ void pc_prune_edges(pc_ctx* c, const State& st, int l) {
   auto release = [&]() {
     ctx_free(c, fut);
     ctx_free(c, unc);
+    ctx_free(c, used);
     ctx_free(c, keep);
     ctx_free(c, counts);
     ctx_free(c, tU);
     ctx_free(c, tW);
     ctx_free(c, tL);
   };
-  if (!fut || !unc || !keep || !counts || !tU || !tW || (c->deferred && !tL)) {
+  if (!fut || !unc || !used || !keep || !counts || !tU || !tW || (c->deferred && !tL)) {
     release();
     throw PcError(PC_ERR_OOM, "pruning: device allocation failed");
   }
@@ -276,8 +328,10 @@ void pc_prune_edges(pc_ctx* c, const State& st, int l) {
   Counters* cn = st.cnt + net.off[l + 1];
   const size_t smem = sizeof(double) * kPruneWarps * (2 * c->mw + Wf);
   const int vgrid = static_cast<int>(std::max<long long>(1, std::min<long long>(4ll * c->num_sms, (V + kPruneWarps - 1) / kPruneWarps)));
-  k_future_signs<<<vgrid, 32 * kPruneWarps, smem, s>>>(net, st, l, c->mw, Wf, static_cast<uint32_t*>(fut),
-                                                      static_cast<unsigned char*>(unc));
+  cudaMemsetAsync(used, 0, V, s);
+  k_mark_edge_ends<<<grid_of(E), 256, 0, s>>>(net, st, l, static_cast<unsigned char*>(used));
+  k_future_signs<<<vgrid, 32 * kPruneWarps, smem, s>>>(net, st, l, c->mw, Wf, static_cast<const unsigned char*>(used),
+                                                      static_cast<uint32_t*>(fut), static_cast<unsigned char*>(unc));
   k_edge_keep<<<grid_of(E), 256, 0, s>>>(net, st, l, Wf, static_cast<const uint32_t*>(fut),
                                          static_cast<const unsigned char*>(unc), static_cast<int*>(keep));
   k_block_count<<<nblocks, kCompactBlock, 0, s>>>(st.g, static_cast<const int*>(keep), nullptr, cn, 0,
@@ -292,7 +346,7 @@ void pc_prune_edges(pc_ctx* c, const State& st, int l) {
   const cudaError_t e = cudaGetLastError();
   release();
   if (e != cudaSuccess) throw PcError(PC_ERR_CUDA, std::string("pruning: ") + cudaGetErrorString(e));
-  c->launches += 6;
+  c->launches += 7;
 }
 
 // After the last step: drops the vertices without an edge and renumbers the
