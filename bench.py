@@ -49,8 +49,8 @@ sys.path.insert(0, ROOT)
 #   k_layer_torus      the D=3 torus workload, 5 k_layer launches
 #   k_layer_d5w40      the D=5 width-40 counting-sweep net (seed 0), 5 launches
 #   k_gemm_tc2_d5w40   the same net's 4 tensor-core layer products
-KERNEL_DRAM = {"sources_sha16": "e83fb753b5871c0b", "k_layer_torus": 183403264, "k_layer_d5w40": 30201796761,
-               "k_gemm_tc2_d5w40": 1222340864}
+KERNEL_DRAM = {"sources_sha16": "6e6aa921f3306f5b", "k_layer_torus": 231117670, "k_layer_d5w40": 30457925529,
+               "k_gemm_tc2_d5w40": 1235692544}
 KERNEL_SOURCES = ("pc_phases.cuh", "pc_core.cu", "pc_device.cuh", "pc_newton.cuh", "pc_gemm_tc.cu", "pc_polish.cu")
 
 METRIC = "vertices+edges/s at D=3 (torus 3-64x4-1, box [-1,1]^3)"

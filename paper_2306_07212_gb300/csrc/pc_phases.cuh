@@ -127,8 +127,10 @@ __device__ __forceinline__ void warp_append(int c, const int4* ent, int4* list, 
 // < e_end moves every value to the exact vertex, z + grad . dx (the step is
 // small, so the float32 gradient adds only ~1e-7 of it).  Each filtered value
 // is written back with its FP64 sign.  The forward pass runs over all
-// (vertex, neuron) pairs of the batch together, tpr threads per pair, so the
-// batch costs one pass of per-layer latency instead of one per vertex.
+// (vertex, neuron) pairs of the batch together, tpr threads per pair (a
+// function of the layer width alone, so results do not depend on how the
+// vertices are batched), so the batch costs one chain of per-layer latency
+// instead of one per vertex.
 // Workspace (dynamic shared memory), rd_layout(P, mw, D, S) bytes:
 struct RdLayout {
   size_t a, an, A, gv, dlt, sig, J, Jn, sc, zl, nz, ok, total;
@@ -215,9 +217,11 @@ __device__ void redecide_batch(const NetDesc& net, const State& st, const long l
     const double* W = net.W64 + net.wofs[k];  // [H][in]
     const float* W32 = net.W32 + net.wofs[k];
     const double* b = net.W64 + net.bofs[k];
+    // tpr (threads per pair) depends on H only, so each value's summation
+    // order, and with it the FP64 result, is the same in any batch
     const int pairs = P * H;
-    int tpr = 32;
-    while (tpr > 1 && pairs * tpr > (int)blockDim.x) tpr >>= 1;
+    int tpr = 16;
+    while (tpr > 1 && H * tpr > (int)blockDim.x) tpr >>= 1;
     const int per = blockDim.x / tpr;
     for (int p0 = 0; p0 < pairs; p0 += per) {
       const int pr = p0 + threadIdx.x / tpr, s = threadIdx.x % tpr;
