@@ -182,3 +182,21 @@ def test_inline_and_deferred_pairing_agree_with_oracle(cuda, D, widths, executio
             assert_same_complex(_gpu_triple(ex), (ref.X, ref.S, ref.E), coord_tol=_tol(box),
                                 what=f"{widths} {pairing} {execution}")
             assert ex.diagnostics()["reruns"] == 0
+
+
+def test_mixed_result_does_not_depend_on_the_launch_grid(cuda):
+    """The persistent kernel (two CTAs per SM) and the stepwise kernels (grids
+    sized to the edge capacity, here from the default and from a large initial
+    capacity) number and batch the new vertices differently; every value, FP64
+    re-decision and polish step is still computed per vertex in a fixed order,
+    so the complex is the same, coordinates to the last bits (a served request
+    must equal the same request run alone)."""
+    net, box = wl.torus_d3()
+    runs = []
+    for execution, vcap, ecap in (("persistent", 0, 0), ("stepwise", 0, 0), ("stepwise", 1 << 20, 1 << 22)):
+        with cuda(precision="mixed", execution=execution, init_vcap=vcap, init_ecap=ecap) as ex:
+            ex.extract(net, box)
+            runs.append(((execution, vcap), _gpu_triple(ex)))
+    (name0, ref), rest = runs[0], runs[1:]
+    for name, r in rest:
+        assert_same_complex(r, ref, coord_tol=1e-12, what=f"{name} against {name0}")
